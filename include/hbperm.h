@@ -1,0 +1,159 @@
+/*
+ * hbperm.h -- C ABI of the GB300 (sm_103a) Householder-aligned permutation
+ * test (Ehara, "Accurate and Efficient Statistical Testing for Word Semantic
+ * Breadth", ACL 2026).
+ *
+ * Problem statement (Sec. 3.1, "Problem setting"): two clouds of unit-norm
+ * token embeddings X (n x d) and Y (m x d); H0 = equal dispersion with the
+ * mean directions allowed to differ.  The test reflects one cloud onto the
+ * other's mean direction (Sec. 3.1, "Householder mean-direction alignment"),
+ * pools Z = X' u Y, draws B relabellings (fixed-space permutation), and
+ * returns p = (1 + #{b : T_b exceeds T_obs})/(B + 1) (Eq. pvalue).
+ *
+ * Conventions for every entry point:
+ *  - Data pointers (X, Y, Z, label bits, T_out) are DEVICE pointers owned by
+ *    the caller, except where an argument says "host".  The library never
+ *    frees caller memory.  hb_perm_test_batched also accepts host memory for
+ *    XY (it then stages the copy itself).
+ *  - Matrices are row-major, one embedding per row, rows contiguous.
+ *    dtype HB_F32 = IEEE binary32, HB_BF16 = bfloat16 (16-bit patterns).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls that fill an hb_result synchronise that stream before
+ *    returning; hb_align and hb_perm_labels return after enqueueing.
+ *  - Errors are status codes; nothing aborts or throws across the ABI.  The
+ *    calling thread's last message is available from hb_last_error().
+ *  - Limits: 1 <= d <= 8192; n, m >= 2 for tests (>= 1 for hb_align);
+ *    n + m <= 2^20; every input value finite with |v| < 16 (unit-normalised
+ *    rows satisfy this); HB_PATH_MIXED additionally needs n + m <= 65536.
+ *
+ * Arithmetic contract (identical results to the FP64/exact CPU oracle):
+ *  - Column and group sums are exact (values widened to a 2^-87 fixed-point
+ *    grid; |v| < 2^-64 counts as 0) and rounded once to FP64.
+ *  - Mean directions, the axis and every reflected row use IEEE FP64 with
+ *    sequential fused multiply-add chains; reflected rows are rounded once to
+ *    the input storage type.
+ *  - Group sums of the B relabellings run on tensor cores (HB_PATH_MIXED) or
+ *    FP32 SIMT (HB_PATH_FP32_PLAIN); every relabelling whose approximate
+ *    statistic falls inside a rigorous error band around the observed one is
+ *    re-decided exactly, so counts and p-values are bit-identical to the
+ *    oracle's.
+ */
+#ifndef HBPERM_H
+#define HBPERM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_INVALID_ARG = 1,  /* bad size, enum, pointer or non-finite/|v|>=16 input      */
+    HB_ERR_DEGENERATE = 2,   /* n<2 or m<2, zero mean vector, observed r = 0 or r >= 1    */
+    HB_ERR_CUDA = 3,         /* a CUDA runtime call failed (message in hb_last_error)      */
+    HB_ERR_OOM = 4,          /* workspace allocation failed                                */
+    HB_ERR_TIMEOUT = 5,      /* a bounded device wait expired; results are not valid       */
+    HB_ERR_UNSUPPORTED = 6   /* valid request outside this build's limits                  */
+} hb_status;
+
+typedef enum { HB_F32 = 0, HB_BF16 = 1 } hb_dtype;
+
+/* Dispersion statistic (Sec. 3.1, Eqs. r, v, tobs).  With r_g = ||sum of
+ * group g|| / n_g the mean resultant length:
+ *   HB_STAT_LOGVOL_VMF  T = log v(G1) - log v(G2), v = 1/g_d(r),
+ *                       g_d(r) = r (d - r^2)/(1 - r^2)   (the paper's log-volume
+ *                       difference; g_d is the approximation of Banerjee et
+ *                       al., JMLR 2005, since the paper does not print it)
+ *   HB_STAT_ONE_MINUS_R2  T = (1 - r_1^2) - (1 - r_2^2)
+ *   HB_STAT_MEAN_COSDIST  T = s_1 - s_2, s_g = (n_g^2 - ||sum||^2)/(n_g (n_g - 1))
+ *                       (mean pairwise cosine distance of unit rows)        */
+typedef enum { HB_STAT_LOGVOL_VMF = 0, HB_STAT_ONE_MINUS_R2 = 1, HB_STAT_MEAN_COSDIST = 2 } hb_stat;
+
+/* Exceedance rule: two-sided |T_b| >= |T_obs| (default), T_b >= T_obs
+ * (Eq. pvalue as printed), or T_b <= T_obs.  Ties count. */
+typedef enum { HB_ALT_TWO_SIDED = 0, HB_ALT_GREATER = 1, HB_ALT_LESS = 2 } hb_alt;
+
+/* HB_PATH_MIXED: exact 16-bit fixed-point slices of Z on tcgen05 tensor
+ * cores (BF16 operands, FP32 accumulators in TMEM).  HB_PATH_FP32_PLAIN: the
+ * paper's Algorithm 2 taken literally (+-1 signs, FP32 SIMT GEMM). */
+typedef enum { HB_PATH_MIXED = 0, HB_PATH_FP32_PLAIN = 1 } hb_path;
+
+typedef struct {
+    uint64_t seed;        /* Philox key (key0 = low 32 bits, key1 = high 32 bits)           */
+    uint32_t stream;      /* Philox counter word 2; 0 = labels depend on (seed, b, n, N)     */
+    int64_t B;            /* number of relabellings (ignored when exhaustive)                */
+    int32_t stat;         /* hb_stat                                                         */
+    int32_t alt;          /* hb_alt                                                          */
+    int32_t align;        /* 1 = Householder alignment (the paper), 0 = naive test            */
+    int32_t reflect_side; /* 0 = reflect X onto Y's direction (the paper), 1 = reflect Y     */
+    int32_t exhaustive;   /* 1 = all C(N, n) splits in colex order, N <= 24; p = count/C     */
+    int32_t path;         /* hb_path                                                         */
+} hb_opts;
+
+typedef struct {
+    double p;                   /* (1 + count)/(B + 1), or count/C when exhaustive          */
+    int64_t count;              /* #{b : T_b exceeds T_obs}                                  */
+    int64_t B_eff;              /* B, or C(N, n) when exhaustive                             */
+    double T_obs;               /* observed statistic (FP64)                                 */
+    double r_x;                 /* observed MRL of group 1 (rows 0..n-1 of Z)                */
+    double r_y;                 /* observed MRL of group 2                                   */
+    int32_t reflection_skipped; /* 1 when no reflection was applied (align = 0 or the mean    */
+                                /*   directions differ by <= 2^-27 in 2-norm)                */
+    int32_t status;             /* hb_status of this pair                                    */
+    int64_t n_rechecked;        /* relabellings re-decided exactly (inside the error band)   */
+    double band_max;            /* largest error band used for a decision                    */
+} hb_result;
+
+typedef struct hb_ctx hb_ctx;
+
+/* Create a context bound to CUDA device `device`.  It owns the device
+ * workspace (grown on demand), pinned staging buffers and captured graphs.
+ * One context must not be used by two threads at once. */
+hb_status hb_ctx_create(hb_ctx **ctx, int device);
+void hb_ctx_destroy(hb_ctx *ctx);
+
+/* Steps 1-3 of Algorithm 1 (Sec. 3.1 alignment equations; Eq.
+ * householder_fast).  Writes the pooled, aligned Z = [X' ; Y] (or [X ; Y']
+ * with reflect_side = 1) as (n + m) x d rows of `dtype` into Z_out (device).
+ * u_out (device, nullable) receives the FP64 axis u (zeros when skipped);
+ * skipped (host, nullable) receives 1 when no reflection was applied, and
+ * forces a stream synchronisation.  align = 0 copies X and Y unchanged. */
+hb_status hb_align(hb_ctx *ctx, const void *X, int64_t n, const void *Y, int64_t m, int64_t d, int32_t dtype,
+                   int32_t align, int32_t reflect_side, void *Z_out, double *u_out, int32_t *skipped, void *stream);
+
+/* The whole test of one pair (Algorithm 1; Algorithm 2 for the
+ * relabellings).  out (host) receives the result.  T_out (device, nullable,
+ * B_eff floats) receives each relabelling's statistic T_b (FP32; exact FP64
+ * value rounded to FP32 for the relabellings re-decided exactly). */
+hb_status hb_perm_test(hb_ctx *ctx, const void *X, int64_t n, const void *Y, int64_t m, int64_t d, int32_t dtype,
+                       const hb_opts *opts, hb_result *out, float *T_out, void *stream);
+
+/* P independent pairs in one grouped launch sequence (the paper's
+ * "Reusability" note, Sec. 3.2: pairs with equal (n, m) share label draws
+ * when opts->stream is equal).  XY (device or host) packs, for each pair p in
+ * order, n[p] rows of X then m[p] rows of Y, each row d values of `dtype`.
+ * n, m (host, P entries) are the group sizes; out (host, P entries) receives
+ * one result per pair.  Returns the first non-OK pair status, else HB_OK;
+ * pairs are independent, so one pair's failure leaves the others valid. */
+hb_status hb_perm_test_batched(hb_ctx *ctx, int64_t P, const void *XY, const int64_t *n, const int64_t *m,
+                               int64_t d, int32_t dtype, const hb_opts *opts, hb_result *out, void *stream);
+
+/* HB-LABEL-v1 label rows for relabellings b0 .. b0+count-1 of a pool of N
+ * with group-1 size n (Sec. 3.2: the sign matrix S with exactly n entries
+ * +1 per row; here bit 1 = group 1).  bits_out (device) is row-major
+ * [count][ceil(N/32)] uint32, position i in bit i%32 of word i/32,
+ * positions >= N zero.  Philox4x32-10 key (seed_lo, seed_hi), counter
+ * (i/4, b_lo, stream_id, b_hi); sequential selection sampling (Knuth,
+ * Algorithm S) with a 32-bit multiply-high. */
+hb_status hb_perm_labels(uint64_t seed, uint32_t stream_id, int64_t n, int64_t N, int64_t b0, int64_t count,
+                         uint32_t *bits_out, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *hb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBPERM_H */

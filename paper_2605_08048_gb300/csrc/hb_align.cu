@@ -1,0 +1,480 @@
+// hb_align.cu -- steps 1-4 of Algorithm 1 on the device.
+//
+//   k_colsum_partial / k_colsum_reduce : exact column sums of X and Y
+//       (Sec. 3.1: x_bar = (1/n) sum x_i), inputs validated on the way
+//   k_axis   : mean directions, v = mu_x - mu_y, u = v/||v|| in FP64
+//       (Sec. 3.1 axis equation; skipped when ||v|| <= 2^-27)
+//   k_reflect: x' = x - 2u(u^T x) per row (Eq. householder_fast), FP64
+//       sequential dot then one FMA per element, rounded once to the storage
+//       type; the other cloud is copied; column maxima for the fixed-point
+//       scales of the mixed path
+//   k_zstats_partial / k_zstats_reduce : exact column totals t of Z and the
+//       group-1 sums of the observed split, the band constants, and (mixed
+//       path) the 16/24-bit fixed-point slices of Z, transposed to
+//       token-contiguous rows for the tensor-core B operand
+//   k_tobs   : observed statistic T_obs from the exact sums (Eq. tobs)
+//
+// The FP64 arithmetic uses explicit __d*_rn / __fma_rn intrinsics so that no
+// contraction or reassociation changes a result.
+#include "hb_launch.cuh"
+
+namespace hb {
+
+// ---------------------------------------------------------------------------
+// Column sums of the inputs (exact), one block per row chunk.
+// ---------------------------------------------------------------------------
+__global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks, int d,
+                                 int dtype, i128 *__restrict__ part, int *__restrict__ bad)
+{
+    const RowChunk ch = chunks[blockIdx.x];
+    const PairMeta pm = meta[ch.pair];
+    const void *base = ch.side ? pm.Y : pm.X;
+    bool ok = true;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        i128 acc = 0;
+        for (int r = 0; r < ch.nrows; ++r) {
+            const uint32_t b = load_f32bits(base, dtype, (int64_t)(ch.row0 + r) * d + j);
+            ok &= valid_f32bits(b);
+            acc += fixed_from_f32bits(b);
+        }
+        part[(int64_t)blockIdx.x * d + j] = acc;
+    }
+    if (!ok) atomicOr(bad + ch.pair, 1);
+}
+
+// s[(p*2 + side)*d + j] = sum over the chunks of (p, side)
+__global__ void k_colsum_reduce(const PairMeta *__restrict__ meta, int P, int d, const i128 *__restrict__ part,
+                                i128 *__restrict__ s)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)P * 2 * d) return;
+    const int j = (int)(idx % d);
+    const int ps = (int)(idx / d);
+    const int p = ps >> 1, side = ps & 1;
+    const PairMeta pm = meta[p];
+    const int c0 = pm.chunk0 + (side ? pm.nchunk_x : 0);
+    const int nc = side ? pm.nchunk_y : pm.nchunk_x;
+    i128 acc = 0;
+    for (int c = 0; c < nc; ++c) acc += part[(int64_t)(c0 + c) * d + j];
+    s[idx] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Axis: one block of 64 threads per pair; dynamic smem 2*d doubles.
+// ---------------------------------------------------------------------------
+__global__ void k_axis(const PairMeta *__restrict__ meta, const RunOpts o, const i128 *__restrict__ s,
+                       const int *__restrict__ bad, PairState *__restrict__ st, double *__restrict__ u)
+{
+    extern __shared__ double sm_axis[];
+    const int p = blockIdx.x;
+    const PairMeta pm = meta[p];
+    const int d = o.d;
+    double *xb = sm_axis, *yb = sm_axis + d;
+    __shared__ double nrm[3];
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        // bad: bit 0 = an input value is non-finite or |v| >= 16 (set on the device),
+        //      bit 1 = n < 2 or m < 2 (set by the host)
+        st[p].status = (bad[p] & 1) ? ST_INVALID : (bad[p] & 2) ? ST_DEGENERATE : ST_OK;
+        st[p].skipped = 1;
+        st[p].count = 0ull;
+        st[p].rechecked = 0ull;
+        st[p].band_max_bits = 0u;
+        skip = 1;
+    }
+    __syncthreads();
+    const bool do_align = o.align && !bad[p];
+    if (!do_align) {
+        for (int j = threadIdx.x; j < d; j += blockDim.x) u[(int64_t)p * d + j] = 0.0;
+        return;
+    }
+    const i128 *sx = s + (int64_t)(2 * p) * d, *sy = sx + d;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        xb[j] = __ddiv_rn(fixed_to_f64(sx[j]), (double)pm.n);
+        yb[j] = __ddiv_rn(fixed_to_f64(sy[j]), (double)pm.m);
+    }
+    __syncthreads();
+    // ||x_bar||^2 and ||y_bar||^2: sequential FMA chains in index order
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const double *v = threadIdx.x ? yb : xb;
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) acc = __fma_rn(v[j], v[j], acc);
+        nrm[threadIdx.x ? 1 : 0] = __dsqrt_rn(acc);
+    }
+    __syncthreads();
+    const double nx = nrm[0], ny = nrm[1];
+    if (!(nx > 0.0) || !(ny > 0.0)) {
+        if (threadIdx.x == 0) st[p].status = ST_DEGENERATE;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) u[(int64_t)p * d + j] = 0.0;
+        return;
+    }
+    for (int j = threadIdx.x; j < d; j += blockDim.x) xb[j] = __dsub_rn(__ddiv_rn(xb[j], nx), __ddiv_rn(yb[j], ny));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) acc = __fma_rn(xb[j], xb[j], acc);
+        const double nv = __dsqrt_rn(acc);
+        nrm[2] = nv;
+        skip = !(nv > 0x1p-27);
+        st[p].skipped = skip;
+    }
+    __syncthreads();
+    const double nv = nrm[2];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) u[(int64_t)p * d + j] = skip ? 0.0 : __ddiv_rn(xb[j], nv);
+}
+
+// ---------------------------------------------------------------------------
+// Reflection / copy into Z, one block (128 threads) per row chunk.
+// ---------------------------------------------------------------------------
+constexpr int RT = 32;  // columns per smem tile of the dot-product phase
+
+template <int DT>
+__device__ __forceinline__ void store_z(void *Z, int64_t idx, double v)
+{
+    if (DT == DT_F32) reinterpret_cast<float *>(Z)[idx] = __double2float_rn(v);
+    else reinterpret_cast<unsigned short *>(Z)[idx] = f64_to_bf16_rn(v);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
+                                                 const RunOpts o, const PairState *__restrict__ st,
+                                                 const double *__restrict__ u, void *__restrict__ Z,
+                                                 unsigned int *__restrict__ colmax)
+{
+    __shared__ float xs[CHUNK_ROWS][RT + 1];
+    __shared__ double us[RT];
+    __shared__ double cs[CHUNK_ROWS];
+    const RowChunk ch = chunks[blockIdx.x];
+    const PairMeta pm = meta[ch.pair];
+    if (st[ch.pair].status != ST_OK) return;
+    const int d = o.d;
+    const void *src = ch.side ? pm.Y : pm.X;
+    const int64_t zrow0 = pm.z_row + (ch.side ? pm.n : 0) + ch.row0;
+    const bool reflect = !st[ch.pair].skipped && (ch.side == o.reflect_side);
+    const double *up = u + (int64_t)ch.pair * d;
+
+    if (reflect) {
+        // c_r = u^T x_r, sequential FMA chain over j = 0..d-1 (one thread per row)
+        double c = 0.0;
+        for (int j0 = 0; j0 < d; j0 += RT) {
+            const int w = min(RT, d - j0);
+            for (int t = threadIdx.x; t < CHUNK_ROWS * RT; t += blockDim.x) {
+                const int r = t / RT, jj = t % RT;
+                float v = 0.0f;
+                if (r < ch.nrows && jj < w)
+                    v = __uint_as_float(load_f32bits(src, DT, (int64_t)(ch.row0 + r) * d + j0 + jj));
+                xs[r][jj] = v;
+            }
+            if (threadIdx.x < RT) us[threadIdx.x] = threadIdx.x < w ? up[j0 + threadIdx.x] : 0.0;
+            __syncthreads();
+            if (threadIdx.x < ch.nrows) {
+                const int r = threadIdx.x;
+                for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], (double)xs[r][jj], c);
+            }
+            __syncthreads();
+        }
+        cs[threadIdx.x] = -2.0 * c;  // exact scaling by -2
+        __syncthreads();
+    }
+    // element pass: z = fl_storage(fma(-2c, u_j, x)) or a copy
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double uj = reflect ? up[j] : 0.0;
+        float mx = 0.0f;
+        for (int r = 0; r < ch.nrows; ++r) {
+            const int64_t si = (int64_t)(ch.row0 + r) * d + j;
+            const int64_t zi = (zrow0 + r) * d + j;
+            const uint32_t xb = load_f32bits(src, DT, si);
+            float zf;
+            if (reflect) {
+                const double zv = __fma_rn(cs[r], uj, (double)__uint_as_float(xb));
+                store_z<DT>(Z, zi, zv);
+                zf = (DT == DT_F32) ? __double2float_rn(zv) : __uint_as_float((uint32_t)f64_to_bf16_rn(zv) << 16);
+            } else {
+                if (DT == DT_F32) reinterpret_cast<uint32_t *>(Z)[zi] = xb;
+                else reinterpret_cast<unsigned short *>(Z)[zi] = (unsigned short)(xb >> 16);
+                zf = __uint_as_float(xb);
+            }
+            mx = fmaxf(mx, fabsf(zf));
+        }
+        if (colmax) atomicMax(colmax + (int64_t)ch.pair * o.d_pad + j, __float_as_uint(mx));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Z statistics and fixed-point slices, one block (256 threads) per row chunk.
+// ---------------------------------------------------------------------------
+constexpr int ZT = 64;  // columns per tile
+
+// scale exponent E of column j: max |z| < 2^E; q_hi = 2^(E-8)
+__device__ __forceinline__ float qhi_from_max(unsigned int maxbits)
+{
+    const int e = (int)((maxbits >> 23) & 0xffu);
+    if (maxbits == 0u) return 1.0f;
+    const int E = e - 126;
+    return ldexpf(1.0f, E - 8);
+}
+
+// Exact hi/lo(/lo2) split of z on its column's fixed-point grid: every step
+// is exact in FP32; `res` is what the slices leave out.
+__device__ __forceinline__ void fixed_split(float z, float qh, int S, float &hi, float &lo, float &lo2, float &res)
+{
+    hi = rintf(z / qh);
+    const float w = __fsub_rn(z, __fmul_rn(hi, qh));
+    const float ql = qh * (1.0f / 256.0f);
+    lo = rintf(w / ql);
+    res = __fsub_rn(w, __fmul_rn(lo, ql));
+    lo2 = 0.0f;
+    if (S == 3) {
+        const float ql2 = ql * (1.0f / 256.0f);
+        lo2 = rintf(res / ql2);
+        res = __fsub_rn(res, __fmul_rn(lo2, ql2));
+    }
+}
+
+// row of the slice matrix holding slice s of column j (tiles of cw columns)
+__device__ __forceinline__ int64_t slice_row(int j, int s, int S, int cw)
+{
+    return (int64_t)(j / cw) * S * cw + (int64_t)s * cw + (j % cw);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restrict__ meta,
+                                                        const RowChunk *__restrict__ chunks, const RunOpts o,
+                                                        const PairState *__restrict__ st, const void *__restrict__ Z,
+                                                        const unsigned int *__restrict__ colmax,
+                                                        i128 *__restrict__ tpart, float *__restrict__ cpart,
+                                                        unsigned short *__restrict__ zq, int64_t zq_ld)
+{
+    __shared__ float zs[CHUNK_ROWS][ZT + 1];
+    __shared__ float qs[ZT];
+    __shared__ i128 acc_s[4][ZT];
+    __shared__ float cacc_s[4][ZT];
+    const RowChunk ch = chunks[blockIdx.x];
+    const PairMeta pm = meta[ch.pair];
+    if (st[ch.pair].status != ST_OK) return;
+    const int d = o.d;
+    const int64_t tok0 = (ch.side ? pm.n : 0) + ch.row0;  // token index within the pair
+    const int64_t zrow0 = pm.z_row + tok0;
+    const bool mixed = (o.path == 0);
+    const int S = o.slices;
+    // the last chunk of the pair also zero-fills the padded tokens of the slices
+    const bool last = ch.side == 1 && ch.row0 + ch.nrows == pm.m;
+    const int npad = last ? pm.N_pad - pm.N : 0;
+
+    for (int j0 = 0; j0 < d; j0 += ZT) {
+        for (int t = threadIdx.x; t < CHUNK_ROWS * ZT; t += blockDim.x) {
+            const int r = t / ZT, jj = t % ZT;
+            float v = 0.0f;
+            if (r < ch.nrows && j0 + jj < d) v = __uint_as_float(load_f32bits(Z, DT, (zrow0 + r) * d + j0 + jj));
+            zs[r][jj] = v;
+        }
+        if (threadIdx.x < ZT) {
+            const int j = j0 + threadIdx.x;
+            qs[threadIdx.x] = (mixed && j < d) ? qhi_from_max(colmax[(int64_t)ch.pair * o.d_pad + j]) : 1.0f;
+        }
+        __syncthreads();
+        // column statistics: 4 threads per column, 32 rows each
+        {
+            const int jj = threadIdx.x % ZT, part = threadIdx.x / ZT;
+            const float qh = qs[jj];
+            i128 acc = 0;
+            float cacc = 0.0f;
+            for (int r = part * 32; r < min(ch.nrows, part * 32 + 32); ++r) {
+                const float z = zs[r][jj];
+                acc += fixed_from_f32bits(__float_as_uint(z));
+                if (mixed) {
+                    float hi, lo, lo2, res;
+                    fixed_split(z, qh, S, hi, lo, lo2, res);
+                    cacc = __fadd_ru(cacc, fabsf(res));
+                } else {
+                    cacc = __fadd_ru(cacc, fabsf(z));
+                }
+            }
+            acc_s[part][jj] = acc;
+            cacc_s[part][jj] = cacc;
+        }
+        // slices, stored token-contiguous (consecutive threads -> consecutive tokens)
+        if (mixed) {
+            for (int t = threadIdx.x; t < ZT * ch.nrows; t += blockDim.x) {
+                const int jj = t / ch.nrows, r = t % ch.nrows;
+                const int j = j0 + jj;
+                if (j >= d) continue;
+                float hi, lo, lo2, res;
+                fixed_split(zs[r][jj], qs[jj], S, hi, lo, lo2, res);
+                const int64_t tok = pm.z_row + tok0 + r;
+                zq[slice_row(j, 0, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+                zq[slice_row(j, 1, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+                if (S == 3) zq[slice_row(j, 2, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(lo2));
+            }
+            for (int t = threadIdx.x; t < ZT * npad; t += blockDim.x) {
+                const int jj = t / npad, k = t % npad;
+                const int j = j0 + jj;
+                if (j >= d) continue;
+                const int64_t tok = pm.z_row + pm.N + k;
+                for (int s = 0; s < S; ++s) zq[slice_row(j, s, S, o.cw) * zq_ld + tok] = 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < ZT && j0 + threadIdx.x < d) {
+            const int jj = threadIdx.x;
+            const i128 a = acc_s[0][jj] + acc_s[1][jj] + acc_s[2][jj] + acc_s[3][jj];
+            const float c =
+                __fadd_ru(__fadd_ru(cacc_s[0][jj], cacc_s[1][jj]), __fadd_ru(cacc_s[2][jj], cacc_s[3][jj]));
+            tpart[(int64_t)blockIdx.x * d + j0 + jj] = a;
+            cpart[(int64_t)blockIdx.x * d + j0 + jj] = c;
+        }
+        __syncthreads();
+    }
+}
+
+// Per (pair, column): exact totals, observed group-1 sums, band constants.
+__global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int P, const RunOpts o,
+                                const PairState *__restrict__ st, const unsigned int *__restrict__ colmax,
+                                const i128 *__restrict__ tpart, const float *__restrict__ cpart,
+                                i128 *__restrict__ t_ex, i128 *__restrict__ s1o, ColConst *__restrict__ cc)
+{
+    const int d = o.d;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)P * o.d_pad) return;
+    const int p = (int)(idx / o.d_pad), j = (int)(idx % o.d_pad);
+    const PairMeta pm = meta[p];
+    ColConst c{0.0f, 0.0f, 0.0f, 0.0f};
+    if (j >= d || st[p].status != ST_OK) {
+        cc[idx] = c;
+        if (j < d) {
+            t_ex[(int64_t)p * d + j] = 0;
+            s1o[(int64_t)p * d + j] = 0;
+        }
+        return;
+    }
+    i128 a = 0, ax = 0;
+    float csum = 0.0f;
+    for (int k = 0; k < pm.nchunk_x + pm.nchunk_y; ++k) {
+        const int64_t q = (int64_t)(pm.chunk0 + k) * d + j;
+        a += tpart[q];
+        if (k < pm.nchunk_x) ax += tpart[q];
+        csum = __fadd_ru(csum, cpart[q]);
+    }
+    t_ex[(int64_t)p * d + j] = a;
+    s1o[(int64_t)p * d + j] = ax;
+    c.t = __double2float_rn(fixed_to_f64(a));
+    if (o.path == 0) {
+        c.q_hi = qhi_from_max(colmax[idx]);
+        c.c = csum;  // sum of |residuals| of the fixed-point slices
+    } else {
+        // sequential FP32 accumulation over K = N_pad tokens: gamma_K = K u / (1 - K u)
+        const float K = (float)pm.N_pad;
+        const float gam = __fdiv_ru(K * U32, 1.0f - K * U32);
+        c.q_hi = 0.5f;
+        c.c = __fmul_ru(gam, csum);
+    }
+    cc[idx] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Observed statistic, one block of 64 threads per pair; dynamic smem 2*d doubles.
+// ---------------------------------------------------------------------------
+__global__ void k_tobs(const PairMeta *__restrict__ meta, const RunOpts o, const i128 *__restrict__ t_ex,
+                       const i128 *__restrict__ s1o, const ColConst *__restrict__ cc, PairState *__restrict__ st)
+{
+    extern __shared__ double sm_tobs[];
+    const int p = blockIdx.x;
+    if (st[p].status != ST_OK) return;
+    const PairMeta pm = meta[p];
+    const int d = o.d;
+    double *a = sm_tobs, *b = sm_tobs + d;
+    __shared__ double q[2];
+    __shared__ float red[2][64];
+    float tn = 0.0f, c2 = 0.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const i128 x = s1o[(int64_t)p * d + j];
+        a[j] = fixed_to_f64(x);
+        b[j] = fixed_to_f64(t_ex[(int64_t)p * d + j] - x);
+        const ColConst c = cc[(int64_t)p * o.d_pad + j];
+        tn = fmaf(c.t, c.t, tn);
+        c2 = __fmaf_ru(c.c, c.c, c2);
+    }
+    red[0][threadIdx.x] = tn;
+    red[1][threadIdx.x] = c2;
+    __syncthreads();
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const double *v = threadIdx.x ? b : a;
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) acc = __fma_rn(v[j], v[j], acc);
+        q[threadIdx.x ? 1 : 0] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float T = 0.0f, C = 0.0f;
+        for (int k = 0; k < 64; ++k) {
+            T += red[0][k];
+            C = __fadd_ru(C, red[1][k]);
+        }
+        const double n = (double)pm.n, m = (double)pm.m, dd = (double)d;
+        const double A1 = group_value_f64(o.stat, q[0], n, dd);
+        const double A2 = group_value_f64(o.stat, q[1], m, dd);
+        PairState &s = st[p];
+        s.A1o = A1;
+        s.A2o = A2;
+        s.To = stat_T_f64(o.stat, A1, A2);
+        s.rx = __dsqrt_rn(__ddiv_rn(q[0], __dmul_rn(n, n)));
+        s.ry = __dsqrt_rn(__ddiv_rn(q[1], __dmul_rn(m, m)));
+        s.tnorm = sqrtf(T) * (1.0f + 1e-4f);
+        s.sumc2 = C * (1.0f + 1e-4f);
+        if (o.stat == STAT_LOGVOL &&
+            (!(q[0] > 0.0) || !(q[1] > 0.0) || !(A1 < INFINITY) || !(A2 < INFINITY)))
+            s.status = ST_DEGENERATE;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned cdiv_(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+void launch_colsum(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, int d, int dtype, i128 *part,
+                   i128 *s, int *bad, cudaStream_t st)
+{
+    k_colsum_partial<<<nch, 256, 0, st>>>(meta, chunks, d, dtype, part, bad);
+    k_colsum_reduce<<<cdiv_((int64_t)P * 2 * d, 256), 256, 0, st>>>(meta, P, d, part, s);
+}
+
+void launch_axis(const PairMeta *meta, int P, const RunOpts &o, const i128 *s, const int *bad, PairState *pst,
+                 double *u, cudaStream_t st)
+{
+    k_axis<<<P, 64, 2 * sizeof(double) * o.d, st>>>(meta, o, s, bad, pst, u);
+}
+
+void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, const RunOpts &o,
+                    const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st)
+{
+    if (o.dtype == DT_F32) k_reflect<DT_F32><<<nch, 128, 0, st>>>(meta, chunks, o, pst, u, Z, colmax);
+    else k_reflect<DT_BF16><<<nch, 128, 0, st>>>(meta, chunks, o, pst, u, Z, colmax);
+}
+
+void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
+                   const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
+                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, cudaStream_t st)
+{
+    if (o.dtype == DT_F32)
+        k_zstats_partial<DT_F32><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+    else
+        k_zstats_partial<DT_BF16><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+    k_zstats_reduce<<<cdiv_((int64_t)P * o.d_pad, 256), 256, 0, st>>>(meta, P, o, pst, colmax, tpart, cpart, t_ex,
+                                                                        s1o, cc);
+}
+
+void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
+                 const ColConst *cc, PairState *pst, cudaStream_t st)
+{
+    k_tobs<<<P, 64, 2 * sizeof(double) * o.d, st>>>(meta, o, t_ex, s1o, cc, pst);
+}
+
+void set_align_attributes()
+{
+    const int big = 200 * 1024;
+    cudaFuncSetAttribute(k_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_tobs, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+}  // namespace hb

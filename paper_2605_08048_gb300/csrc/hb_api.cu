@@ -1,0 +1,619 @@
+// hb_api.cu -- the C ABI (include/hbperm.h): argument checking, per-pair
+// metadata, the device workspace, and the launch sequence of one test batch:
+//
+//   colsum -> axis -> reflect -> zstats -> tobs -> labels -> GEMM+epilogue
+//          -> exact recheck -> finalize -> one device-to-host copy
+//
+// Everything between the metadata upload and the result download runs on the
+// caller's stream with no host round trip.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hb_launch.cuh"
+#include "hbperm.h"
+
+namespace hb {
+// mixed (tensor-core) path, hb_mixed.cu
+struct MixedArgs {
+    const PairMeta *meta;
+    const PairMeta *meta_host;
+    int P;
+    RunOpts o;
+    PairState *st;
+    const ColConst *cc;
+    const uint32_t *bits;
+    const unsigned short *zq;
+    int64_t zq_ld;      // tokens per slice row
+    int64_t zq_rows;    // slice rows
+    RecheckItem *list;
+    unsigned int *n_items;
+    unsigned int cap;
+    unsigned int *overflow;
+    unsigned int *timeout;
+    float *T_out;
+    void *work;         // device scratch for the schedule
+    size_t work_bytes;
+    int sms;
+};
+size_t mixed_work_bytes(int P, const PairMeta *meta_host);
+cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
+}  // namespace hb
+
+using namespace hb;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static hb_status fail(hb_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(HB_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char *hb_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct hb_ctx {
+    int device = 0;
+    int sms = 0;
+    void *ws = nullptr;
+    size_t ws_cap = 0;
+    void *stage = nullptr;  // pinned host staging
+    size_t stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool attrs_set = false;
+};
+
+extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
+{
+    if (!out) return fail(HB_ERR_INVALID_ARG, "ctx pointer is NULL");
+    int count = 0;
+    CK(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(HB_ERR_INVALID_ARG, "device %d out of range", device);
+    CK(cudaSetDevice(device));
+    hb_ctx *c = new hb_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete c;
+        return fail(HB_ERR_CUDA, "cudaEventCreate failed");
+    }
+    *out = c;
+    g_err.clear();
+    return HB_OK;
+}
+
+extern "C" void hb_ctx_destroy(hb_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stage_done) {
+        cudaEventSynchronize(c->stage_done);
+        cudaEventDestroy(c->stage_done);
+    }
+    if (c->ws) cudaFree(c->ws);
+    if (c->stage) cudaFreeHost(c->stage);
+    delete c;
+}
+
+static hb_status ensure_ws(hb_ctx *c, size_t bytes)
+{
+    if (bytes <= c->ws_cap) return HB_OK;
+    if (c->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_cap = 0;
+    }
+    const size_t want = bytes + (bytes >> 3);
+    if (cudaMalloc(&c->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HB_ERR_OOM, "device workspace of %zu bytes could not be allocated", want);
+    }
+    c->ws_cap = want;
+    return HB_OK;
+}
+
+static hb_status ensure_stage(hb_ctx *c, size_t bytes)
+{
+    if (c->stage_done) cudaEventSynchronize(c->stage_done);  // previous upload finished reading it
+    if (bytes <= c->stage_cap) return HB_OK;
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    const size_t want = std::max<size_t>(bytes * 2, 1 << 20);
+    if (cudaMallocHost(&c->stage, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HB_ERR_OOM, "pinned staging of %zu bytes could not be allocated", want);
+    }
+    c->stage_cap = want;
+    return HB_OK;
+}
+
+static void set_attrs(hb_ctx *c)
+{
+    if (c->attrs_set) return;
+    set_kernel_attributes();
+    c->attrs_set = true;
+}
+
+// ---------------------------------------------------------------------------
+// workspace carving
+// ---------------------------------------------------------------------------
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int64_t binom64(int64_t N, int64_t k)
+{
+    if (k < 0 || k > N) return 0;
+    if (k > N - k) k = N - k;
+    int64_t c = 1;
+    for (int64_t i = 1; i <= k; ++i) c = c * (N - k + i) / i;
+    return c;
+}
+
+static inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Plan {
+    int P;
+    RunOpts o;
+    std::vector<PairMeta> meta;
+    std::vector<RowChunk> chunks;
+    std::vector<int> init_bad;
+    int64_t total_rows_pad = 0, total_label_words = 0, total_B = 0;
+    int max_Bpad = 0, max_W = 0, max_N = 0;
+};
+
+static hb_status validate_common(int64_t d, int32_t dtype)
+{
+    if (d < 1 || d > 8192) return fail(HB_ERR_INVALID_ARG, "d = %lld outside [1, 8192]", (long long)d);
+    if (dtype != HB_F32 && dtype != HB_BF16) return fail(HB_ERR_INVALID_ARG, "dtype %d unknown", dtype);
+    return HB_OK;
+}
+
+static hb_status validate_opts(const hb_opts *op)
+{
+    if (!op) return fail(HB_ERR_INVALID_ARG, "opts is NULL");
+    if (op->stat < 0 || op->stat > 2) return fail(HB_ERR_INVALID_ARG, "stat %d unknown", op->stat);
+    if (op->alt < 0 || op->alt > 2) return fail(HB_ERR_INVALID_ARG, "alt %d unknown", op->alt);
+    if (op->reflect_side != 0 && op->reflect_side != 1)
+        return fail(HB_ERR_INVALID_ARG, "reflect_side %d unknown", op->reflect_side);
+    if (op->path != HB_PATH_MIXED && op->path != HB_PATH_FP32_PLAIN)
+        return fail(HB_ERR_INVALID_ARG, "path %d unknown", op->path);
+    if (!op->exhaustive && (op->B < 1 || op->B > 0x7fffffffLL))
+        return fail(HB_ERR_INVALID_ARG, "B = %lld outside [1, 2^31)", (long long)op->B);
+    return HB_OK;
+}
+
+// Builds the per-pair metadata.  X/Y pointers filled by the caller.
+static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
+                           const hb_opts &op, bool align_only, bool want_T)
+{
+    pl.P = (int)P;
+    RunOpts &o = pl.o;
+    memset(&o, 0, sizeof o);
+    o.seed = op.seed;
+    o.stream = op.stream;
+    o.stat = op.stat;
+    o.alt = op.alt;
+    o.align = op.align ? 1 : 0;
+    o.reflect_side = op.reflect_side;
+    o.exhaustive = op.exhaustive ? 1 : 0;
+    o.path = align_only ? 1 : op.path;
+    o.d = (int)d;
+    o.dtype = dtype;
+    o.want_T = want_T ? 1 : 0;
+    if (o.path == HB_PATH_MIXED) {
+        o.slices = dtype == HB_F32 ? 3 : 2;
+        o.cw = o.slices == 2 ? 128 : 64;
+        o.d_pad = (int)rup(d, o.cw);
+    } else {
+        o.slices = 0;
+        o.cw = 128;
+        o.d_pad = (int)d;
+    }
+    pl.meta.resize(P);
+    pl.init_bad.assign(P, 0);
+    pl.chunks.clear();
+    int64_t zrow = 0, lab = 0, tb = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        const int64_t np = n[p], mp = m[p];
+        if (np < 1 || mp < 1) return fail(HB_ERR_INVALID_ARG, "pair %lld: n = %lld, m = %lld", (long long)p,
+                                          (long long)np, (long long)mp);
+        const int64_t N = np + mp;
+        if (N > (1 << 20)) return fail(HB_ERR_UNSUPPORTED, "pair %lld: n + m = %lld > 2^20", (long long)p, (long long)N);
+        if (!align_only && o.path == HB_PATH_MIXED && N > 65536)
+            return fail(HB_ERR_UNSUPPORTED, "pair %lld: the mixed path needs n + m <= 65536", (long long)p);
+        if (!align_only && op.exhaustive && N > 24)
+            return fail(HB_ERR_UNSUPPORTED, "pair %lld: exhaustive mode needs n + m <= 24", (long long)p);
+        PairMeta &pm = pl.meta[p];
+        memset(&pm, 0, sizeof pm);
+        pm.n = (int)np;
+        pm.m = (int)mp;
+        pm.N = (int)N;
+        pm.N_pad = (int)rup(N, 64);
+        pm.z_row = zrow;
+        zrow += pm.N_pad;
+        pm.W = (int)((N + 31) / 32);
+        if (!align_only) {
+            pm.B = op.exhaustive ? binom64(N, np) : op.B;
+            pm.B_pad = (int)rup(pm.B, 128);
+            pm.lab_off = lab;
+            lab += (int64_t)pm.W * pm.B_pad;
+            pm.T_off = want_T ? tb : -1;
+            tb += pm.B;
+            if (np < 2 || mp < 2) pl.init_bad[p] = 2;
+        }
+        pm.chunk0 = (int)pl.chunks.size();
+        for (int64_t r = 0; r < np; r += CHUNK_ROWS)
+            pl.chunks.push_back(RowChunk{(int)p, 0, (int)r, (int)std::min<int64_t>(CHUNK_ROWS, np - r)});
+        pm.nchunk_x = (int)pl.chunks.size() - pm.chunk0;
+        for (int64_t r = 0; r < mp; r += CHUNK_ROWS)
+            pl.chunks.push_back(RowChunk{(int)p, 1, (int)r, (int)std::min<int64_t>(CHUNK_ROWS, mp - r)});
+        pm.nchunk_y = (int)pl.chunks.size() - pm.chunk0 - pm.nchunk_x;
+        pl.max_Bpad = std::max(pl.max_Bpad, pm.B_pad);
+        pl.max_W = std::max(pl.max_W, pm.W);
+        pl.max_N = std::max(pl.max_N, pm.N);
+    }
+    pl.total_rows_pad = zrow;
+    pl.total_label_words = lab;
+    pl.total_B = tb;
+    return HB_OK;
+}
+
+// Device buffers of one run.
+struct Bufs {
+    PairMeta *meta;
+    RowChunk *chunks;
+    int *bad;
+    PairState *st;
+    i128 *part;
+    i128 *s;
+    double *u;
+    void *Z;
+    unsigned int *colmax;
+    float *cpart;
+    i128 *t_ex, *s1o;
+    ColConst *cc;
+    unsigned short *zq;
+    uint32_t *bits;
+    RecheckItem *list;
+    unsigned int *counters;  // [0] recheck items, [1] overflow, [2] timeout
+    double *scratch;
+    PairOut *out;
+    void *xy;
+    void *mixed_work;
+};
+
+static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool own_Z, size_t xy_bytes,
+                    unsigned int cap, int rgrid, size_t mixed_bytes)
+{
+    const int P = pl.P;
+    const int d = pl.o.d;
+    const size_t nch = pl.chunks.size();
+    const size_t esz = pl.o.dtype == HB_F32 ? 4 : 2;
+    b.meta = cv.take<PairMeta>(P);
+    b.chunks = cv.take<RowChunk>(nch);
+    b.bad = cv.take<int>(P);
+    b.st = cv.take<PairState>(P);
+    b.part = cv.take<i128>(nch * d);
+    b.s = cv.take<i128>((size_t)P * 2 * d);
+    b.u = cv.take<double>((size_t)P * d);
+    b.Z = own_Z ? (void *)cv.take<char>((size_t)pl.total_rows_pad * d * esz) : nullptr;
+    b.colmax = cv.take<unsigned int>((size_t)P * pl.o.d_pad);
+    b.xy = xy_bytes ? (void *)cv.take<char>(xy_bytes) : nullptr;
+    if (!align_only) {
+        b.cpart = cv.take<float>(nch * d);
+        b.t_ex = cv.take<i128>((size_t)P * d);
+        b.s1o = cv.take<i128>((size_t)P * d);
+        b.cc = cv.take<ColConst>((size_t)P * pl.o.d_pad);
+        b.zq = pl.o.path == HB_PATH_MIXED
+                   ? cv.take<unsigned short>((size_t)pl.o.slices * pl.o.d_pad * pl.total_rows_pad)
+                   : nullptr;
+        b.bits = cv.take<uint32_t>(pl.total_label_words);
+        b.list = cv.take<RecheckItem>(cap);
+        b.counters = cv.take<unsigned int>(4);
+        b.scratch = cv.take<double>((size_t)rgrid * 2 * d);
+        b.out = cv.take<PairOut>(P);
+        b.mixed_work = mixed_bytes ? (void *)cv.take<char>(mixed_bytes) : nullptr;
+    }
+    return cv.off;
+}
+
+static inline unsigned int cdiv(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+// The whole launch sequence.  Xp/Yp: device pointers per pair.
+static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
+                     bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
+                     cudaStream_t s, std::vector<PairOut> &out)
+{
+    set_attrs(c);
+    const int P = pl.P;
+    const RunOpts o = pl.o;
+    const int d = o.d;
+    const size_t esz = o.dtype == HB_F32 ? 4 : 2;
+    const bool mixed = !align_only && o.path == HB_PATH_MIXED;
+    unsigned int cap = (unsigned int)std::min<int64_t>(
+        (int64_t)1 << 30, (mixed ? pl.total_B / 256 : pl.total_B / 16) + 4096);
+    const size_t mixed_bytes = mixed ? mixed_work_bytes(P, pl.meta.data()) : 0;
+
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 4 * c->sms));
+        Bufs b{};
+        Carve plan_cv(nullptr);
+        const size_t need = carve(plan_cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid, mixed_bytes);
+        hb_status hs = ensure_ws(c, need);
+        if (hs != HB_OK) return hs;
+        Carve cv(c->ws);
+        carve(cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid, mixed_bytes);
+        void *Z = Z_out ? Z_out : b.Z;
+
+        // input staging (host memory) and pair pointers
+        if (xy_host) {
+            CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
+            for (int p = 0; p < P; ++p) {
+                pl.meta[p].X = (const char *)b.xy + (size_t)xy_row_off[p] * d * esz;
+                pl.meta[p].Y = (const char *)pl.meta[p].X + (size_t)pl.meta[p].n * d * esz;
+            }
+        }
+        // metadata upload through pinned staging
+        const size_t mbytes = sizeof(PairMeta) * P, cbytes = sizeof(RowChunk) * pl.chunks.size(),
+                     bbytes = sizeof(int) * P;
+        hs = ensure_stage(c, mbytes + cbytes + bbytes + 64);
+        if (hs != HB_OK) return hs;
+        char *hs_ = (char *)c->stage;
+        memcpy(hs_, pl.meta.data(), mbytes);
+        memcpy(hs_ + mbytes, pl.chunks.data(), cbytes);
+        memcpy(hs_ + mbytes + cbytes, pl.init_bad.data(), bbytes);
+        CK(cudaMemcpyAsync(b.meta, hs_, mbytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(b.chunks, hs_ + mbytes, cbytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(b.bad, hs_ + mbytes + cbytes, bbytes, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(c->stage_done, s));
+        if (mixed || o.path == HB_PATH_MIXED) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
+        if (!align_only) CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
+        if (mixed && o.d_pad != d)
+            CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
+
+        const unsigned int nch = (unsigned int)pl.chunks.size();
+        // steps 1-3
+        launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
+        launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
+        unsigned int *colmax = (o.path == HB_PATH_MIXED) ? b.colmax : nullptr;
+        launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, colmax, s);
+        CK(cudaGetLastError());
+
+        if (align_only) {
+            if (u_out) CK(cudaMemcpyAsync(u_out, b.u, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
+            if (skipped_out) {
+                PairState hst;
+                CK(cudaMemcpyAsync(&hst, b.st, sizeof hst, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (hst.status != ST_OK)
+                    return fail((hb_status)hst.status, "alignment failed (status %d)", hst.status);
+                *skipped_out = hst.skipped;
+            }
+            return HB_OK;
+        }
+
+        // step 4: Z statistics, fixed-point slices, T_obs
+        const int64_t zq_ld = pl.total_rows_pad;
+        launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o,
+                      b.cc, s);
+        launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
+        CK(cudaGetLastError());
+
+        // step 5: labels, group sums + statistic + band, exact recheck
+        launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, s);
+        CK(cudaGetLastError());
+        if (mixed) {
+            MixedArgs ma{};
+            ma.meta = b.meta;
+            ma.meta_host = pl.meta.data();
+            ma.P = P;
+            ma.o = o;
+            ma.st = b.st;
+            ma.cc = b.cc;
+            ma.bits = b.bits;
+            ma.zq = b.zq;
+            ma.zq_ld = zq_ld;
+            ma.zq_rows = (int64_t)o.slices * o.d_pad;
+            ma.list = b.list;
+            ma.n_items = b.counters;
+            ma.cap = cap;
+            ma.overflow = b.counters + 1;
+            ma.timeout = b.counters + 2;
+            ma.T_out = T_out;
+            ma.work = b.mixed_work;
+            ma.work_bytes = mixed_bytes;
+            ma.sms = c->sms;
+            std::string err;
+            const cudaError_t e = launch_mixed(ma, s, err);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
+                            "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
+            }
+        } else {
+            launch_plain(b.meta, P, pl.max_Bpad, o, b.st, Z, b.cc, b.bits, b.list, b.counters, cap, b.counters + 1,
+                         T_out, s);
+        }
+        CK(cudaGetLastError());
+        launch_recheck(rgrid, sizeof(uint32_t) * pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.bits, b.list, b.counters,
+                       cap, b.scratch, T_out, s);
+        launch_finalize(b.meta, P, o, b.st, b.out, s);
+        CK(cudaGetLastError());
+
+        // one copy back: results and the counters
+        hs = ensure_stage(c, sizeof(PairOut) * P + 64);
+        if (hs != HB_OK) return hs;
+        char *h = (char *)c->stage;
+        CK(cudaMemcpyAsync(h, b.counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 64, b.out, sizeof(PairOut) * P, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const unsigned int *cnt = (const unsigned int *)h;
+        if (cnt[2]) return fail(HB_ERR_TIMEOUT, "a bounded device wait expired in the mixed path");
+        if (cnt[1]) {
+            cap = (unsigned int)std::min<int64_t>((int64_t)1 << 30, pl.total_B + 64);
+            continue;  // recheck list overflowed: rerun with room for every relabelling
+        }
+        out.assign((PairOut *)(h + 64), (PairOut *)(h + 64) + P);
+        return HB_OK;
+    }
+    return fail(HB_ERR_CUDA, "recheck list kept overflowing");
+}
+
+static void fill_result(const PairOut &r, hb_result *o)
+{
+    o->p = r.p;
+    o->count = r.count;
+    o->B_eff = r.B_eff;
+    o->T_obs = r.T_obs;
+    o->r_x = r.r_x;
+    o->r_y = r.r_y;
+    o->reflection_skipped = r.skipped;
+    o->status = r.status;
+    o->n_rechecked = r.rechecked;
+    o->band_max = r.band_max;
+}
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+extern "C" hb_status hb_perm_labels(uint64_t seed, uint32_t stream_id, int64_t n, int64_t N, int64_t b0,
+                                    int64_t count, uint32_t *bits_out, void *stream)
+{
+    if (N < 1 || N > (1 << 20) || n < 0 || n > N || b0 < 0 || count < 0 || b0 + count > ((int64_t)1 << 40))
+        return fail(HB_ERR_INVALID_ARG, "bad label request n=%lld N=%lld b0=%lld count=%lld", (long long)n,
+                    (long long)N, (long long)b0, (long long)count);
+    if (count == 0) return HB_OK;
+    if (!bits_out) return fail(HB_ERR_INVALID_ARG, "bits_out is NULL");
+    launch_labels_rows(seed, stream_id, (int)n, (int)N, b0, count, bits_out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" hb_status hb_align(hb_ctx *c, const void *X, int64_t n, const void *Y, int64_t m, int64_t d, int32_t dtype,
+                              int32_t align, int32_t reflect_side, void *Z_out, double *u_out, int32_t *skipped,
+                              void *stream)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    if (!X || !Y || !Z_out) return fail(HB_ERR_INVALID_ARG, "X, Y and Z_out must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    if (reflect_side != 0 && reflect_side != 1) return fail(HB_ERR_INVALID_ARG, "reflect_side %d", reflect_side);
+    CK(cudaSetDevice(c->device));
+    hb_opts op{};
+    op.align = align;
+    op.reflect_side = reflect_side;
+    op.path = HB_PATH_FP32_PLAIN;
+    op.B = 1;
+    Plan pl;
+    hs = make_plan(pl, 1, &n, &m, d, dtype, op, true, false);
+    if (hs != HB_OK) return hs;
+    pl.meta[0].X = X;
+    pl.meta[0].Y = Y;
+    std::vector<PairOut> out;
+    return run(c, pl, nullptr, 0, nullptr, true, Z_out, u_out, skipped, nullptr, (cudaStream_t)stream, out);
+}
+
+extern "C" hb_status hb_perm_test(hb_ctx *c, const void *X, int64_t n, const void *Y, int64_t m, int64_t d,
+                                  int32_t dtype, const hb_opts *opts, hb_result *res, float *T_out, void *stream)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    if (!X || !Y || !res) return fail(HB_ERR_INVALID_ARG, "X, Y and out must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    memset(res, 0, sizeof *res);
+    if (n < 2 || m < 2) {
+        res->status = HB_ERR_DEGENERATE;
+        return fail(HB_ERR_DEGENERATE, "n = %lld and m = %lld must both be >= 2", (long long)n, (long long)m);
+    }
+    CK(cudaSetDevice(c->device));
+    Plan pl;
+    hs = make_plan(pl, 1, &n, &m, d, dtype, *opts, false, T_out != nullptr);
+    if (hs != HB_OK) return hs;
+    pl.meta[0].X = X;
+    pl.meta[0].Y = Y;
+    std::vector<PairOut> out;
+    hs = run(c, pl, nullptr, 0, nullptr, false, nullptr, nullptr, nullptr, T_out, (cudaStream_t)stream, out);
+    if (hs != HB_OK) return hs;
+    fill_result(out[0], res);
+    if (out[0].status != HB_OK) return fail((hb_status)out[0].status, "test failed with status %d", out[0].status);
+    g_err.clear();
+    return HB_OK;
+}
+
+extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m,
+                                          int64_t d, int32_t dtype, const hb_opts *opts, hb_result *res, void *stream)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    if (P < 1 || P > (1 << 24)) return fail(HB_ERR_INVALID_ARG, "P = %lld", (long long)P);
+    if (!XY || !n || !m || !res) return fail(HB_ERR_INVALID_ARG, "XY, n, m and out must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    CK(cudaSetDevice(c->device));
+    Plan pl;
+    hs = make_plan(pl, P, n, m, d, dtype, *opts, false, false);
+    if (hs != HB_OK) return hs;
+    const size_t esz = dtype == HB_F32 ? 4 : 2;
+    std::vector<int64_t> off(P + 1, 0);
+    for (int64_t p = 0; p < P; ++p) off[p + 1] = off[p] + n[p] + m[p];
+    cudaPointerAttributes attr{};
+    const cudaError_t ae = cudaPointerGetAttributes(&attr, XY);
+    if (ae != cudaSuccess) cudaGetLastError();
+    const bool on_device = ae == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    const size_t xy_bytes = (size_t)off[P] * d * esz;
+    for (int64_t p = 0; p < P; ++p) {
+        pl.meta[p].X = (const char *)XY + (size_t)off[p] * d * esz;
+        pl.meta[p].Y = (const char *)pl.meta[p].X + (size_t)n[p] * d * esz;
+    }
+    std::vector<PairOut> out;
+    hs = run(c, pl, on_device ? nullptr : XY, on_device ? 0 : xy_bytes, off.data(), false, nullptr, nullptr, nullptr,
+             nullptr, (cudaStream_t)stream, out);
+    if (hs != HB_OK) return hs;
+    hb_status first = HB_OK;
+    for (int64_t p = 0; p < P; ++p) {
+        fill_result(out[p], &res[p]);
+        if (out[p].status != HB_OK && first == HB_OK) first = (hb_status)out[p].status;
+    }
+    if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
+    g_err.clear();
+    return HB_OK;
+}

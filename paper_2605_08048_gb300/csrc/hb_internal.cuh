@@ -1,0 +1,331 @@
+// hb_internal.cuh -- device helpers and launch metadata shared by the hbperm
+// kernels (sm_103a).  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hb {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+enum : int32_t { ST_OK = 0, ST_INVALID = 1, ST_DEGENERATE = 2, ST_TIMEOUT = 5 };
+enum : int32_t { DT_F32 = 0, DT_BF16 = 1 };
+enum : int32_t { STAT_LOGVOL = 0, STAT_R2 = 1, STAT_COSDIST = 2 };
+enum : int32_t { ALT_TWO = 0, ALT_GREATER = 1, ALT_LESS = 2 };
+
+// Per-pair launch metadata, built on the host.
+struct PairMeta {
+    const void *X;      // device pointer to n rows
+    const void *Y;      // device pointer to m rows
+    int64_t z_row;      // first row of this pair in Z (rows padded to 64)
+    int64_t lab_off;    // first word of this pair's label block [W][B_pad]
+    int64_t B;          // relabellings (C(N, n) when exhaustive)
+    int64_t T_off;      // offset of this pair's T_b values in T_out, -1 = none
+    int32_t n, m, N, N_pad;
+    int32_t W;          // 32-bit label words per relabelling
+    int32_t B_pad;      // B rounded up to 128
+    int32_t chunk0;     // first row chunk of this pair (X side then Y side)
+    int32_t nchunk_x;   // row chunks of the X side
+    int32_t nchunk_y;   // row chunks of the Y side
+    int32_t pad_;
+};
+
+// A chunk of at most CHUNK_ROWS consecutive rows of one side of one pair.
+constexpr int CHUNK_ROWS = 128;
+struct RowChunk {
+    int32_t pair;
+    int32_t side;   // 0 = rows of X (group 1 of the observed split), 1 = rows of Y
+    int32_t row0;   // first row within the side
+    int32_t nrows;
+};
+
+// Per-pair state written by the device.
+struct PairState {
+    int32_t status;
+    int32_t skipped;
+    double A1o, A2o, To;     // observed per-group values and T_obs (FP64, exact path)
+    double rx, ry;
+    float tnorm;             // ||t|| (FP32) for the error band
+    float sumc2;             // sum_j c_j^2 of the per-column band constants
+    unsigned long long count;
+    unsigned long long rechecked;
+    unsigned int band_max_bits;  // float bits of the largest band (atomicMax)
+    int32_t pad_;
+};
+
+// Per-column constants of one pair for the fast paths.
+struct ColConst {
+    float q_hi;   // fixed-point scale of the hi slice (mixed path); 0.5 for plain
+    float t;      // column total of Z, rounded to FP32
+    float c;      // band constant: residual sum R_j (mixed) or gamma_K * sum|z| (plain)
+    float pad_;
+};
+
+// Shared launch options (flattened hb_opts).
+struct RunOpts {
+    uint64_t seed;
+    uint32_t stream;
+    int32_t stat, alt, align, reflect_side, exhaustive, path;
+    int32_t d, d_pad, dtype, slices;
+    int32_t want_T;
+    int32_t cw;      // z-columns per tensor-core column tile (128 for 2 slices, 64 for 3)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Values and the exact 2^-87 fixed-point grid.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t load_f32bits(const void *base, int dtype, int64_t idx)
+{
+    if (dtype == DT_F32) return __ldg(reinterpret_cast<const uint32_t *>(base) + idx);
+    return uint32_t(__ldg(reinterpret_cast<const unsigned short *>(base) + idx)) << 16;
+}
+
+// finite and |v| < 16
+__device__ __forceinline__ bool valid_f32bits(uint32_t b)
+{
+    return ((b >> 23) & 0xffu) < 131u;
+}
+
+// v * 2^87 exactly; |v| < 2^-64 gives 0.
+__device__ __forceinline__ i128 fixed_from_f32bits(uint32_t b)
+{
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e < 63u) return 0;
+    const uint64_t mant = (b & 0x7fffffu) | 0x800000u;
+    const uint32_t sh = e - 63u;
+    u128 m = (u128)mant << sh;
+    return (b >> 31) ? -(i128)m : (i128)m;
+}
+
+__device__ __forceinline__ double pow2d(int e)  // 2^e for -1022 <= e <= 1023
+{
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Exact integer -> FP64, round-to-nearest-even.
+__device__ __forceinline__ double i128_to_f64_rn(i128 v)
+{
+    if (v == 0) return 0.0;
+    const bool neg = v < 0;
+    const u128 a = neg ? (u128)0 - (u128)v : (u128)v;
+    const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    double r;
+    if (msb <= 52) {
+        r = __ull2double_rn(lo);  // exact
+    } else {
+        const int sh = msb - 52;
+        uint64_t top = (uint64_t)(a >> sh);
+        const u128 rem = a & (((u128)1 << sh) - 1);
+        const u128 half = (u128)1 << (sh - 1);
+        if (rem > half || (rem == half && (top & 1ull))) top += 1ull;
+        r = __dmul_rn(__ull2double_rn(top), pow2d(sh));  // both exact
+    }
+    return neg ? -r : r;
+}
+
+__device__ __forceinline__ double fixed_to_f64(i128 v)
+{
+    return __dmul_rn(i128_to_f64_rn(v), pow2d(-87));
+}
+
+__device__ __forceinline__ double f32bits_to_f64(uint32_t b)
+{
+    return (double)__uint_as_float(b);
+}
+
+// Right shift with round-to-nearest-even, s >= 1.
+__device__ __forceinline__ uint64_t rshift_rne(uint64_t v, int s)
+{
+    if (s >= 64) return 0ull;  // v < 2^53 here, so v / 2^s < 1/2
+    const uint64_t q = v >> s;
+    const uint64_t rem = v & ((1ull << s) - 1ull);
+    const uint64_t half = 1ull << (s - 1);
+    return (rem > half || (rem == half && (q & 1ull))) ? q + 1ull : q;
+}
+
+// FP64 -> BF16 bit pattern, one rounding to nearest-even (finite input).
+__device__ __forceinline__ uint16_t f64_to_bf16_rn(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint16_t sign = (uint16_t)((b >> 48) & 0x8000u);
+    const int ebits = (int)((b >> 52) & 0x7ff);
+    if (ebits == 0) return sign;  // zero or below 2^-1022: rounds to zero in BF16
+    const int e = ebits - 1023;
+    const uint64_t sig = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    if (e >= -126) {
+        uint64_t s8 = rshift_rne(sig, 45);  // 8 significant bits, may round up to 256
+        int ee = e;
+        if (s8 == 256ull) {
+            s8 = 128ull;
+            ++ee;
+        }
+        if (ee > 127) return (uint16_t)(sign | 0x7f80u);
+        return (uint16_t)(sign | (uint16_t)((ee + 127) << 7) | (uint16_t)(s8 & 0x7fu));
+    }
+    // subnormal BF16: value / 2^-133 = sig * 2^(e + 81)
+    const uint64_t k = rshift_rne(sig, -(e + 81));
+    return (uint16_t)(sign | (uint16_t)k);  // k == 128 encodes the smallest normal
+}
+
+// ---------------------------------------------------------------------------
+// Exact-path statistic (FP64, correctly rounded operations only).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double group_value_f64(int stat, double q, double ng, double d)
+{
+    const double ng2 = __dmul_rn(ng, ng);
+    if (stat == STAT_LOGVOL) {
+        const double rr = __ddiv_rn(q, ng2);
+        const double r = __dsqrt_rn(rr);
+        const double den = __dsub_rn(1.0, rr);
+        if (!(den > 0.0)) return __longlong_as_double(0x7ff0000000000000ll);
+        return __ddiv_rn(__dmul_rn(r, __dsub_rn(d, rr)), den);
+    }
+    if (stat == STAT_R2) return __dsub_rn(1.0, __ddiv_rn(q, ng2));
+    return __ddiv_rn(__dsub_rn(ng2, q), __dmul_rn(ng, __dsub_rn(ng, 1.0)));
+}
+
+__device__ __forceinline__ double stat_T_f64(int stat, double A1, double A2)
+{
+    if (stat == STAT_LOGVOL) return __dsub_rn(log(A2), log(A1));
+    return __dsub_rn(A1, A2);
+}
+
+__device__ __forceinline__ int exceeds_f64(int stat, int alt, double A1b, double A2b, double A1o, double A2o)
+{
+    if (stat == STAT_LOGVOL) {
+        if (alt == ALT_GREATER) return __dmul_rn(A2b, A1o) >= __dmul_rn(A2o, A1b);
+        if (alt == ALT_LESS) return __dmul_rn(A2b, A1o) <= __dmul_rn(A2o, A1b);
+        const double hib = A1b > A2b ? A1b : A2b, lob = A1b > A2b ? A2b : A1b;
+        const double hio = A1o > A2o ? A1o : A2o, loo = A1o > A2o ? A2o : A1o;
+        return __dmul_rn(hib, loo) >= __dmul_rn(hio, lob);
+    }
+    const double Tb = __dsub_rn(A1b, A2b), To = __dsub_rn(A1o, A2o);
+    if (alt == ALT_GREATER) return Tb >= To;
+    if (alt == ALT_LESS) return Tb <= To;
+    return fabs(Tb) >= fabs(To);
+}
+
+// ---------------------------------------------------------------------------
+// Fast-path decision with a rigorous error band (FP32).
+//   q1, q2   : approximate squared group-sum norms
+//   dq1, dq2 : bounds on |q_hat - q| (exact q of the relabelling)
+// Returns +1 (exceeds), 0 (does not), -1 (inside the band: decide exactly).
+// ---------------------------------------------------------------------------
+constexpr float U32 = 5.9604645e-8f;  // 2^-24
+
+__device__ __forceinline__ float logvol_phi_band(float q, float dq, float ng, float d, float *phi)
+{
+    // phi = log g(r), r = sqrt(q)/ng.  |dphi/dq| <= h(r)/(2q) with
+    // h(r) = 1 + 2 r^2/(1 - r^2) an upper bound of d log g / d log r.
+    const float ng2 = ng * ng;
+    const float rr = q / ng2;
+    const float r = sqrtf(rr);
+    const float den = 1.0f - rr;
+    const float g = r * (d - rr) / den;
+    *phi = logf(g);
+    const float qlo = q - dq, qhi = q + dq;
+    const float rrhi = qhi / ng2;
+    if (!(qlo > 0.0f) || !(rrhi < 0.999f) || !(den > 0.0f) || !(g > 0.0f)) return INFINITY;
+    const float h = 1.0f + 2.0f * rrhi / (1.0f - rrhi);
+    const float lin = h * dq / (2.0f * qlo);
+    const float ev = 16.0f * U32 * (2.0f + 2.0f / (1.0f - rrhi)) + 4.0f * U32 * fabsf(*phi);
+    return lin + ev;
+}
+
+__device__ __forceinline__ int fast_decide(int stat, int alt, float d, float n, float m, float q1, float q2, float dq1,
+                                           float dq2, float To, float *T_hat, float *band)
+{
+    float T, eps;
+    if (stat == STAT_LOGVOL) {
+        float p1, p2;
+        const float e1 = logvol_phi_band(q1, dq1, n, d, &p1);
+        const float e2 = logvol_phi_band(q2, dq2, m, d, &p2);
+        T = p2 - p1;
+        eps = e1 + e2 + 4.0f * U32 * fabsf(T);
+    } else if (stat == STAT_R2) {
+        const float a = q1 / (n * n), b = q2 / (m * m);
+        T = b - a;
+        eps = dq1 / (n * n) + dq2 / (m * m) + 8.0f * U32 * (a + b + fabsf(T));
+    } else {
+        const float a = (n * n - q1) / (n * (n - 1.0f)), b = (m * m - q2) / (m * (m - 1.0f));
+        T = a - b;
+        eps = dq1 / (n * (n - 1.0f)) + dq2 / (m * (m - 1.0f)) +
+              8.0f * U32 * ((n * n + q1) / (n * (n - 1.0f)) + (m * m + q2) / (m * (m - 1.0f)) + fabsf(T));
+    }
+    float D;
+    if (alt == ALT_GREATER) D = T - To;
+    else if (alt == ALT_LESS) D = To - T;
+    else D = fabsf(T) - fabsf(To);
+    // rounding of To to FP32, of the subtraction, and a factor 2 of safety
+    eps = 2.0f * (eps + 4.0f * U32 * (fabsf(T) + fabsf(To))) + 1e-30f;
+    *T_hat = T;
+    *band = eps;
+    if (!(eps < INFINITY) || D != D) return -1;
+    if (D > eps) return 1;
+    if (D < -eps) return 0;
+    return -1;
+}
+
+// Bound on |q_hat - q| given the accumulated terms (see the design notes):
+//   E    = sum_j |sigma_hat_j| c_j      (first-order term of the per-column bounds)
+//   q    = q_hat of this group, qa/qb = both groups, tnorm = ||t||,
+//   sumc2 = sum_j c_j^2, chain = rounding-chain length of the q accumulation.
+__device__ __forceinline__ float q_bound(float E, float q, float q1, float q2, float tnorm, float sumc2, float chain)
+{
+    const float s = sqrtf(q), s1 = sqrtf(q1), s2 = sqrtf(q2);
+    const float first = 2.0f * E * (1.0f + (chain + 8.0f) * U32) + 4.0f * U32 * s * (tnorm + s1 + s2);
+    const float second = 2.0f * sumc2 + 24.0f * U32 * U32 * (tnorm * tnorm + q1 + q2);
+    return (first + second + chain * U32 * q) * (1.0f + 1e-3f);
+}
+
+// A relabelling whose fast-path decision fell inside its error band.
+struct alignas(8) RecheckItem {
+    int32_t pair;
+    uint32_t b;
+};
+
+__device__ __forceinline__ void push_recheck(RecheckItem *list, unsigned int *n_items, unsigned int cap,
+                                             unsigned int *overflow, int p, uint32_t b)
+{
+    const unsigned int k = atomicAdd(n_items, 1u);
+    if (k < cap) list[k] = RecheckItem{p, b};
+    else atomicExch(overflow, 1u);
+}
+
+// Per-pair result copied back to the host.
+struct PairOut {
+    double p;
+    int64_t count;
+    int64_t B_eff;
+    double T_obs, r_x, r_y;
+    int32_t skipped, status;
+    int64_t rechecked;
+    double band_max;
+};
+
+// Iteration cap of every bounded device spin-wait.
+constexpr long long SPIN_LIMIT = 1ll << 26;
+
+}  // namespace hb

@@ -1,0 +1,35 @@
+// hb_launch.cuh -- host-side launchers of the hbperm kernels (one per kernel
+// family; each lives in the translation unit that defines its kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hb_internal.cuh"
+
+namespace hb {
+void launch_colsum(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, int d, int dtype, i128 *part,
+                   i128 *s, int *bad, cudaStream_t st);
+void launch_axis(const PairMeta *meta, int P, const RunOpts &o, const i128 *s, const int *bad, PairState *pst,
+                 double *u, cudaStream_t st);
+void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, const RunOpts &o,
+                    const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st);
+void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
+                   const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
+                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, cudaStream_t st);
+void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
+                 const ColConst *cc, PairState *pst, cudaStream_t st);
+void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
+                        cudaStream_t st);
+void launch_labels_pipeline(const PairMeta *meta, const PairState *pst, int P, int max_Bpad, const RunOpts &o,
+                            uint32_t *bits, cudaStream_t st);
+void launch_plain(const PairMeta *meta, int P, int max_Bpad, const RunOpts &o, PairState *pst, const void *Z,
+                  const ColConst *cc, const uint32_t *bits, RecheckItem *list, unsigned int *n_items,
+                  unsigned int cap, unsigned int *overflow, float *T_out, cudaStream_t st);
+void launch_recheck(int grid, size_t smem, const PairMeta *meta, const RunOpts &o, PairState *pst, const void *Z,
+                    const i128 *t_ex, const uint32_t *bits, const RecheckItem *list, const unsigned int *n_items,
+                    unsigned int cap, double *scratch, float *T_out, cudaStream_t st);
+void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairState *pst, PairOut *out,
+                     cudaStream_t st);
+void set_kernel_attributes();
+void set_align_attributes();
+}  // namespace hb

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libhbperm.so (include/hbperm.h).
+
+Argument marshalling only: every step of the test runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The binding refuses to
+run when the compiled library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhbperm.so")
+
+HB_OK, HB_ERR_INVALID_ARG, HB_ERR_DEGENERATE, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TIMEOUT, HB_ERR_UNSUPPORTED = range(7)
+HB_F32, HB_BF16 = 0, 1
+HB_STAT_LOGVOL_VMF, HB_STAT_ONE_MINUS_R2, HB_STAT_MEAN_COSDIST = 0, 1, 2
+HB_ALT_TWO_SIDED, HB_ALT_GREATER, HB_ALT_LESS = 0, 1, 2
+HB_PATH_MIXED, HB_PATH_FP32_PLAIN = 0, 1
+
+
+class HbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hbperm status {status}: {msg}")
+        self.status = status
+
+
+class hb_opts(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("stream", C.c_uint32),
+        ("B", C.c_int64),
+        ("stat", C.c_int32),
+        ("alt", C.c_int32),
+        ("align", C.c_int32),
+        ("reflect_side", C.c_int32),
+        ("exhaustive", C.c_int32),
+        ("path", C.c_int32),
+    ]
+
+
+class hb_result(C.Structure):
+    _fields_ = [
+        ("p", C.c_double),
+        ("count", C.c_int64),
+        ("B_eff", C.c_int64),
+        ("T_obs", C.c_double),
+        ("r_x", C.c_double),
+        ("r_y", C.c_double),
+        ("reflection_skipped", C.c_int32),
+        ("status", C.c_int32),
+        ("n_rechecked", C.c_int64),
+        ("band_max", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Loads libhbperm.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhbperm.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, u64, u32 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_uint32
+        L.hb_ctx_create.argtypes = [C.POINTER(vp), C.c_int]
+        L.hb_ctx_create.restype = C.c_int
+        L.hb_ctx_destroy.argtypes = [vp]
+        L.hb_ctx_destroy.restype = None
+        L.hb_align.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, i32, vp, vp, C.POINTER(i32), vp]
+        L.hb_align.restype = C.c_int
+        L.hb_perm_test.argtypes = [vp, vp, i64, vp, i64, i64, i32, C.POINTER(hb_opts), C.POINTER(hb_result), vp, vp]
+        L.hb_perm_test.restype = C.c_int
+        L.hb_perm_test_batched.argtypes = [vp, i64, vp, vp, vp, i64, i32, C.POINTER(hb_opts), C.POINTER(hb_result), vp]
+        L.hb_perm_test_batched.restype = C.c_int
+        L.hb_perm_labels.argtypes = [u64, u32, i64, i64, i64, i64, vp, vp]
+        L.hb_perm_labels.restype = C.c_int
+        L.hb_last_error.argtypes = []
+        L.hb_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != HB_OK:
+        raise HbError(st, lib().hb_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return HB_F32
+    if t.dtype == torch.bfloat16:
+        return HB_BF16
+    raise TypeError("embeddings must be torch.float32 or torch.bfloat16")
+
+
+def _dev(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_opts(B=9999, seed=0, stream=0, stat=HB_STAT_LOGVOL_VMF, alt=HB_ALT_TWO_SIDED, align=1, reflect_side=0,
+              exhaustive=0, path=HB_PATH_MIXED) -> hb_opts:
+    return hb_opts(seed, stream, B, stat, alt, align, reflect_side, exhaustive, path)
+
+
+class Context:
+    """Owns an hb_ctx (device workspace, pinned staging)."""
+
+    def __init__(self, device: int | None = None):
+        dev = torch.cuda.current_device() if device is None else device
+        self.device = dev
+        h = C.c_void_p()
+        _check(lib().hb_ctx_create(C.byref(h), dev))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().hb_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hb_align(ctx: Context, X: torch.Tensor, Y: torch.Tensor, align=1, reflect_side=0, stream=None):
+    """Returns (Z [n+m][d] same dtype, u [d] float64, skipped)."""
+    dt = _dtype_code(X)
+    assert Y.dtype == X.dtype and X.shape[1] == Y.shape[1]
+    n, d = X.shape
+    m = Y.shape[0]
+    Z = torch.empty((n + m, d), dtype=X.dtype, device=X.device)
+    u = torch.empty(d, dtype=torch.float64, device=X.device)
+    sk = C.c_int32(0)
+    _check(lib().hb_align(ctx.handle, _dev(X), n, _dev(Y), m, d, dt, align, reflect_side, _dev(Z), _dev(u),
+                          C.byref(sk), _stream(stream)))
+    return Z, u, int(sk.value)
+
+
+def hb_perm_test(ctx: Context, X: torch.Tensor, Y: torch.Tensor, opts: hb_opts, want_T=False, stream=None,
+                 check=True):
+    """Returns (result dict, T_b float32 tensor or None)."""
+    dt = _dtype_code(X)
+    n, d = X.shape
+    m = Y.shape[0]
+    res = hb_result()
+    T = None
+    Tp = C.c_void_p(None)
+    if want_T:
+        from math import comb
+        Beff = comb(n + m, n) if opts.exhaustive else opts.B
+        T = torch.full((Beff,), float("nan"), dtype=torch.float32, device=X.device)
+        Tp = _dev(T)
+    st = lib().hb_perm_test(ctx.handle, _dev(X), n, _dev(Y), m, d, dt, C.byref(opts), C.byref(res), Tp,
+                            _stream(stream))
+    if check:
+        _check(st)
+    return res.as_dict(), T
+
+
+def hb_perm_test_batched(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, stream=None, check=True):
+    """XY packs, per pair, n[p] rows of X then m[p] rows of Y (device or host
+    tensor).  Returns a list of result dicts."""
+    dt = _dtype_code(XY)
+    d = XY.shape[1]
+    if not XY.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    P = len(n)
+    na = (C.c_int64 * P)(*[int(v) for v in n])
+    ma = (C.c_int64 * P)(*[int(v) for v in m])
+    res = (hb_result * P)()
+    st = lib().hb_perm_test_batched(ctx.handle, P, C.c_void_p(XY.data_ptr()), na, ma, d, dt, C.byref(opts), res,
+                                    _stream(stream))
+    if check:
+        _check(st)
+    return [r.as_dict() for r in res]
+
+
+def hb_perm_labels(seed: int, stream_id: int, n: int, N: int, b0: int, count: int, device=None, stream=None):
+    """HB-LABEL-v1 rows [count][ceil(N/32)] as an int32 tensor (bit patterns)."""
+    W = (N + 31) // 32
+    out = torch.zeros((count, W), dtype=torch.int32, device=device or torch.cuda.current_device())
+    _check(lib().hb_perm_labels(seed, stream_id, n, N, b0, count, _dev(out), _stream(stream)))
+    return out
+
+
+def declared_symbols(header: str | None = None):
+    """Function names declared in include/hbperm.h."""
+    import re
+    header = header or os.path.join(os.path.dirname(_HERE), "include", "hbperm.h")
+    src = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:hb_status|void|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))

@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/hbperm.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import shutil
+
+import pytest
+
+from paper_2605_08048_gb300 import hbperm as H
+
+
+@pytest.fixture(scope="module")
+def built():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    from paper_2605_08048_gb300 import build
+    return build.build()
+
+
+def test_exports_every_declared_symbol(built):
+    names = H.declared_symbols()
+    assert {"hb_align", "hb_perm_test", "hb_perm_test_batched", "hb_perm_labels"} <= set(names)
+    lib = ctypes.CDLL(built)
+    missing = [s for s in names if not hasattr(lib, s)]
+    assert not missing
+
+
+def test_header_struct_layouts_match_binding(tmp_path):
+    """sizeof/offsetof of the header's structs, compiled by the C compiler,
+    equal the ctypes mirrors of the binding."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    fields_o = [f for f, _ in H.hb_opts._fields_]
+    fields_r = [f for f, _ in H.hb_result._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "hbperm.h"', "int main(void){",
+            'printf("%zu %zu\\n", sizeof(hb_opts), sizeof(hb_result));']
+    body += [f'printf("%zu\\n", offsetof(hb_opts, {f}));' for f in fields_o]
+    body += [f'printf("%zu\\n", offsetof(hb_result, {f}));' for f in fields_r]
+    body += ["return 0;}"]
+    src.write_text("\n".join(body))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals[0] == ctypes.sizeof(H.hb_opts) and vals[1] == ctypes.sizeof(H.hb_result)
+    offs = [getattr(H.hb_opts, f).offset for f in fields_o] + [getattr(H.hb_result, f).offset for f in fields_r]
+    assert vals[2:] == offs
+
+
+def test_binding_refuses_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(H, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(H, "_lib", None)
+    with pytest.raises(RuntimeError):
+        H.lib()
