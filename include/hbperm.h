@@ -149,6 +149,20 @@ hb_status hb_perm_test_batched(hb_ctx *ctx, int64_t P, const void *XY, const int
 hb_status hb_perm_labels(uint64_t seed, uint32_t stream_id, int64_t n, int64_t N, int64_t b0, int64_t count,
                          uint32_t *bits_out, void *stream);
 
+/* Tracing: per-stage device timing of the calls made on this context, from
+ * CUDA events recorded on the caller's stream between the stages (off by
+ * default; enabling it adds no synchronisation). */
+hb_status hb_ctx_set_timing(hb_ctx *ctx, int32_t enable);
+
+/* Stage durations of the last hb_perm_test / hb_perm_test_batched call on
+ * this context, in milliseconds (ms_out, host, 6 floats): [0] alignment
+ * (column sums, axis, reflection), [1] Z statistics, fixed-point slices and
+ * T_obs, [2] label draws, [3] group-sum GEMM with the fused statistic
+ * epilogue, [4] exact recheck, [5] p-values and the result copy.
+ * n_launches (host, nullable) receives the kernel launches of that call.
+ * HB_ERR_INVALID_ARG if timing was not enabled for that call. */
+hb_status hb_ctx_stage_times(hb_ctx *ctx, float *ms_out, int32_t *n_launches);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *hb_last_error(void);
 

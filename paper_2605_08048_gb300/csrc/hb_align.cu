@@ -215,17 +215,19 @@ __device__ __forceinline__ float qhi_from_max(unsigned int maxbits)
 }
 
 // Exact hi/lo(/lo2) split of z on its column's fixed-point grid: every step
-// is exact in FP32; `res` is what the slices leave out.
+// is exact in FP32; `res` is what the slices leave out.  |z| < 256 q_hi, so
+// |hi| <= 256; the lower slices use grids 512x finer, so |lo|, |lo2| <= 256.
+// Integers of magnitude <= 256 are exact in BF16.
 __device__ __forceinline__ void fixed_split(float z, float qh, int S, float &hi, float &lo, float &lo2, float &res)
 {
     hi = rintf(z / qh);
     const float w = __fsub_rn(z, __fmul_rn(hi, qh));
-    const float ql = qh * (1.0f / 256.0f);
+    const float ql = qh * (1.0f / 512.0f);
     lo = rintf(w / ql);
     res = __fsub_rn(w, __fmul_rn(lo, ql));
     lo2 = 0.0f;
     if (S == 3) {
-        const float ql2 = ql * (1.0f / 256.0f);
+        const float ql2 = ql * (1.0f / 512.0f);
         lo2 = rintf(res / ql2);
         res = __fsub_rn(res, __fmul_rn(lo2, ql2));
     }

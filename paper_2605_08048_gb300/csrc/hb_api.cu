@@ -19,33 +19,6 @@
 #include "hb_launch.cuh"
 #include "hbperm.h"
 
-namespace hb {
-// mixed (tensor-core) path, hb_mixed.cu
-struct MixedArgs {
-    const PairMeta *meta;
-    const PairMeta *meta_host;
-    int P;
-    RunOpts o;
-    PairState *st;
-    const ColConst *cc;
-    const uint32_t *bits;
-    const unsigned short *zq;
-    int64_t zq_ld;      // tokens per slice row
-    int64_t zq_rows;    // slice rows
-    RecheckItem *list;
-    unsigned int *n_items;
-    unsigned int cap;
-    unsigned int *overflow;
-    unsigned int *timeout;
-    float *T_out;
-    void *work;         // device scratch for the schedule
-    size_t work_bytes;
-    int sms;
-};
-size_t mixed_work_bytes(int P, const PairMeta *meta_host);
-cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
-}  // namespace hb
-
 using namespace hb;
 
 // ---------------------------------------------------------------------------
@@ -72,6 +45,10 @@ static hb_status fail(hb_status st, const char *fmt, ...)
 
 extern "C" const char *hb_last_error(void) { return g_err.c_str(); }
 
+struct hb_ctx;
+extern "C" hb_status hb_ctx_set_timing(hb_ctx *c, int32_t enable);
+extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_launches);
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -84,7 +61,18 @@ struct hb_ctx {
     size_t stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
     bool attrs_set = false;
+    // tracing: events between the stages of the last call
+    bool timing = false;
+    bool last_timed = false;
+    cudaEvent_t tev[7] = {};
+    float last_ms[6] = {};
+    int last_launches = 0;
 };
+
+static void mark(hb_ctx *c, int k, cudaStream_t s)
+{
+    if (c->timing) cudaEventRecord(c->tev[k], s);
+}
 
 extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
 {
@@ -113,6 +101,8 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
         cudaEventSynchronize(c->stage_done);
         cudaEventDestroy(c->stage_done);
     }
+    for (int k = 0; k < 7; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFreeHost(c->stage);
     delete c;
@@ -193,6 +183,7 @@ struct Plan {
     std::vector<PairMeta> meta;
     std::vector<RowChunk> chunks;
     std::vector<int> init_bad;
+    std::vector<WorkItem> items;  // (pair, 128-relabelling tile), costliest pairs first
     int64_t total_rows_pad = 0, total_label_words = 0, total_B = 0;
     int max_Bpad = 0, max_W = 0, max_N = 0;
 };
@@ -270,7 +261,8 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         pm.W = (int)((N + 31) / 32);
         if (!align_only) {
             pm.B = op.exhaustive ? binom64(N, np) : op.B;
-            pm.B_pad = (int)rup(pm.B, 128);
+            // the mixed path works on groups of MIXED_CLUSTER tiles of 128 relabellings
+            pm.B_pad = (int)rup(pm.B, o.path == HB_PATH_MIXED ? 128 * MIXED_CLUSTER : 128);
             pm.lab_off = lab;
             lab += (int64_t)pm.W * pm.B_pad;
             pm.T_off = want_T ? tb : -1;
@@ -291,6 +283,16 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
     pl.total_rows_pad = zrow;
     pl.total_label_words = lab;
     pl.total_B = tb;
+    pl.items.clear();
+    if (!align_only && o.path == HB_PATH_MIXED) {
+        std::vector<int> order(P);
+        for (int64_t p = 0; p < P; ++p) order[p] = (int)p;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return pl.meta[a].N_pad > pl.meta[b].N_pad; });
+        for (int p : order)
+            if (pl.init_bad[p] == 0)
+                for (int g = 0; g < pl.meta[p].B_pad / (128 * MIXED_CLUSTER); ++g) pl.items.push_back(WorkItem{p, g});
+    }
     return HB_OK;
 }
 
@@ -315,11 +317,11 @@ struct Bufs {
     double *scratch;
     PairOut *out;
     void *xy;
-    void *mixed_work;
+    WorkItem *items;
 };
 
 static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool own_Z, size_t xy_bytes,
-                    unsigned int cap, int rgrid, size_t mixed_bytes)
+                    unsigned int cap, int rgrid)
 {
     const int P = pl.P;
     const int d = pl.o.d;
@@ -348,12 +350,11 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
         b.counters = cv.take<unsigned int>(4);
         b.scratch = cv.take<double>((size_t)rgrid * 2 * d);
         b.out = cv.take<PairOut>(P);
-        b.mixed_work = mixed_bytes ? (void *)cv.take<char>(mixed_bytes) : nullptr;
+        b.items = pl.o.path == HB_PATH_MIXED ? cv.take<WorkItem>(pl.items.size()) : nullptr;
     }
     return cv.off;
 }
 
-static inline unsigned int cdiv(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
 
 // The whole launch sequence.  Xp/Yp: device pointers per pair.
 static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
@@ -368,17 +369,16 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
     const bool mixed = !align_only && o.path == HB_PATH_MIXED;
     unsigned int cap = (unsigned int)std::min<int64_t>(
         (int64_t)1 << 30, (mixed ? pl.total_B / 256 : pl.total_B / 16) + 4096);
-    const size_t mixed_bytes = mixed ? mixed_work_bytes(P, pl.meta.data()) : 0;
 
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 4 * c->sms));
         Bufs b{};
         Carve plan_cv(nullptr);
-        const size_t need = carve(plan_cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid, mixed_bytes);
+        const size_t need = carve(plan_cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid);
         hb_status hs = ensure_ws(c, need);
         if (hs != HB_OK) return hs;
         Carve cv(c->ws);
-        carve(cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid, mixed_bytes);
+        carve(cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid);
         void *Z = Z_out ? Z_out : b.Z;
 
         // input staging (host memory) and pair pointers
@@ -391,8 +391,8 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         }
         // metadata upload through pinned staging
         const size_t mbytes = sizeof(PairMeta) * P, cbytes = sizeof(RowChunk) * pl.chunks.size(),
-                     bbytes = sizeof(int) * P;
-        hs = ensure_stage(c, mbytes + cbytes + bbytes + 64);
+                     bbytes = sizeof(int) * P, ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0;
+        hs = ensure_stage(c, mbytes + cbytes + bbytes + ibytes + 64);
         if (hs != HB_OK) return hs;
         char *hs_ = (char *)c->stage;
         memcpy(hs_, pl.meta.data(), mbytes);
@@ -401,6 +401,10 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         CK(cudaMemcpyAsync(b.meta, hs_, mbytes, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(b.chunks, hs_ + mbytes, cbytes, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(b.bad, hs_ + mbytes + cbytes, bbytes, cudaMemcpyHostToDevice, s));
+        if (ibytes) {
+            memcpy(hs_ + mbytes + cbytes + bbytes, pl.items.data(), ibytes);
+            CK(cudaMemcpyAsync(b.items, hs_ + mbytes + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, s));
+        }
         CK(cudaEventRecord(c->stage_done, s));
         if (mixed || o.path == HB_PATH_MIXED) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
         if (!align_only) CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
@@ -409,6 +413,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
 
         const unsigned int nch = (unsigned int)pl.chunks.size();
         // steps 1-3
+        mark(c, 0, s);
         launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
         launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
         unsigned int *colmax = (o.path == HB_PATH_MIXED) ? b.colmax : nullptr;
@@ -430,18 +435,20 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
 
         // step 4: Z statistics, fixed-point slices, T_obs
         const int64_t zq_ld = pl.total_rows_pad;
+        mark(c, 1, s);
         launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o,
                       b.cc, s);
         launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
         CK(cudaGetLastError());
 
         // step 5: labels, group sums + statistic + band, exact recheck
+        mark(c, 2, s);
         launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, s);
+        mark(c, 3, s);
         CK(cudaGetLastError());
         if (mixed) {
             MixedArgs ma{};
             ma.meta = b.meta;
-            ma.meta_host = pl.meta.data();
             ma.P = P;
             ma.o = o;
             ma.st = b.st;
@@ -456,8 +463,8 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             ma.overflow = b.counters + 1;
             ma.timeout = b.counters + 2;
             ma.T_out = T_out;
-            ma.work = b.mixed_work;
-            ma.work_bytes = mixed_bytes;
+            ma.items = b.items;
+            ma.n_work = (int)pl.items.size();
             ma.sms = c->sms;
             std::string err;
             const cudaError_t e = launch_mixed(ma, s, err);
@@ -471,8 +478,10 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
                          T_out, s);
         }
         CK(cudaGetLastError());
+        mark(c, 4, s);
         launch_recheck(rgrid, sizeof(uint32_t) * pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.bits, b.list, b.counters,
                        cap, b.scratch, T_out, s);
+        mark(c, 5, s);
         launch_finalize(b.meta, P, o, b.st, b.out, s);
         CK(cudaGetLastError());
 
@@ -482,6 +491,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         char *h = (char *)c->stage;
         CK(cudaMemcpyAsync(h, b.counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h + 64, b.out, sizeof(PairOut) * P, cudaMemcpyDeviceToHost, s));
+        mark(c, 6, s);
         CK(cudaStreamSynchronize(s));
         const unsigned int *cnt = (const unsigned int *)h;
         if (cnt[2]) return fail(HB_ERR_TIMEOUT, "a bounded device wait expired in the mixed path");
@@ -490,6 +500,12 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             continue;  // recheck list overflowed: rerun with room for every relabelling
         }
         out.assign((PairOut *)(h + 64), (PairOut *)(h + 64) + P);
+        c->last_timed = c->timing;
+        if (c->timing) {
+            for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], c->tev[k], c->tev[k + 1]);
+        }
+        // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck + finalize
+        c->last_launches = 10 + (int)((P + 65534) / 65535) * (mixed ? 1 : 2);
         return HB_OK;
     }
     return fail(HB_ERR_CUDA, "recheck list kept overflowing");
@@ -615,5 +631,25 @@ extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, 
     }
     if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
     g_err.clear();
+    return HB_OK;
+}
+
+extern "C" hb_status hb_ctx_set_timing(hb_ctx *c, int32_t enable)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    if (enable && !c->tev[0]) {
+        CK(cudaSetDevice(c->device));
+        for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&c->tev[k]));
+    }
+    c->timing = enable != 0;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_launches)
+{
+    if (!c || !ms_out) return fail(HB_ERR_INVALID_ARG, "ctx and ms_out must be non-NULL");
+    if (!c->last_timed) return fail(HB_ERR_INVALID_ARG, "timing was not enabled for the last call");
+    for (int k = 0; k < 6; ++k) ms_out[k] = c->last_ms[k];
+    if (n_launches) *n_launches = c->last_launches;
     return HB_OK;
 }

@@ -250,7 +250,10 @@ __device__ __forceinline__ float logvol_phi_band(float q, float dq, float ng, fl
     if (!(qlo > 0.0f) || !(rrhi < 0.999f) || !(den > 0.0f) || !(g > 0.0f)) return INFINITY;
     const float h = 1.0f + 2.0f * rrhi / (1.0f - rrhi);
     const float lin = h * dq / (2.0f * qlo);
-    const float ev = 16.0f * U32 * (2.0f + 2.0f / (1.0f - rrhi)) + 4.0f * U32 * fabsf(*phi);
+    // FP32 evaluation of phi(q_hat): rr (2 roundings), sqrt, d - rr, 1 - rr (its
+    // error amplified by rr/(1 - rr)), product and quotient give a relative
+    // error of g below (7 + 2 rr/(1 - rr)) u; logf adds at most 1 ulp of phi.
+    const float ev = 1.1f * U32 * (7.0f + 2.0f * rrhi / (1.0f - rrhi)) + 2.2f * U32 * fabsf(*phi);
     return lin + ev;
 }
 
@@ -263,11 +266,11 @@ __device__ __forceinline__ int fast_decide(int stat, int alt, float d, float n, 
         const float e1 = logvol_phi_band(q1, dq1, n, d, &p1);
         const float e2 = logvol_phi_band(q2, dq2, m, d, &p2);
         T = p2 - p1;
-        eps = e1 + e2 + 4.0f * U32 * fabsf(T);
+        eps = e1 + e2 + U32 * fabsf(T);
     } else if (stat == STAT_R2) {
         const float a = q1 / (n * n), b = q2 / (m * m);
         T = b - a;
-        eps = dq1 / (n * n) + dq2 / (m * m) + 8.0f * U32 * (a + b + fabsf(T));
+        eps = dq1 / (n * n) + dq2 / (m * m) + 3.0f * U32 * (a + b + fabsf(T));
     } else {
         const float a = (n * n - q1) / (n * (n - 1.0f)), b = (m * m - q2) / (m * (m - 1.0f));
         T = a - b;
@@ -278,8 +281,9 @@ __device__ __forceinline__ int fast_decide(int stat, int alt, float d, float n, 
     if (alt == ALT_GREATER) D = T - To;
     else if (alt == ALT_LESS) D = To - T;
     else D = fabsf(T) - fabsf(To);
-    // rounding of To to FP32, of the subtraction, and a factor 2 of safety
-    eps = 2.0f * (eps + 4.0f * U32 * (fabsf(T) + fabsf(To))) + 1e-30f;
+    // rounding of To to FP32 and of the subtraction; a factor 1.5 covers the
+    // second-order terms the first-order bounds above leave out
+    eps = 1.5f * (eps + 2.0f * U32 * (fabsf(T) + fabsf(To))) + 1e-30f;
     *T_hat = T;
     *band = eps;
     if (!(eps < INFINITY) || D != D) return -1;
@@ -294,10 +298,12 @@ __device__ __forceinline__ int fast_decide(int stat, int alt, float d, float n, 
 //   sumc2 = sum_j c_j^2, chain = rounding-chain length of the q accumulation.
 __device__ __forceinline__ float q_bound(float E, float q, float q1, float q2, float tnorm, float sumc2, float chain)
 {
+    // per column: |sigma_hat_g - sigma_g| <= c_j + u (|t_j| + |s1_j| + |s2_j| + |s_g,j|) (1 + 2u),
+    // so 2 sum_j |sigma_hat_g| e_j <= 2E + 2.01 u (s (||t|| + s1 + s2) + q) by Cauchy-Schwarz
     const float s = sqrtf(q), s1 = sqrtf(q1), s2 = sqrtf(q2);
-    const float first = 2.0f * E * (1.0f + (chain + 8.0f) * U32) + 4.0f * U32 * s * (tnorm + s1 + s2);
-    const float second = 2.0f * sumc2 + 24.0f * U32 * U32 * (tnorm * tnorm + q1 + q2);
-    return (first + second + chain * U32 * q) * (1.0f + 1e-3f);
+    const float first = 2.0f * E * (1.0f + (chain + 8.0f) * U32) + 2.01f * U32 * (s * (tnorm + s1 + s2) + q);
+    const float second = 2.0f * sumc2 + 10.0f * U32 * U32 * (tnorm * tnorm + q1 + q2 + q);
+    return (first + second + chain * U32 * q) * (1.0f + 1e-4f);
 }
 
 // A relabelling whose fast-path decision fell inside its error band.

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "hb_internal.cuh"
 
 namespace hb {
@@ -30,6 +32,37 @@ void launch_recheck(int grid, size_t smem, const PairMeta *meta, const RunOpts &
                     unsigned int cap, double *scratch, float *T_out, cudaStream_t st);
 void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairState *pst, PairOut *out,
                      cudaStream_t st);
+// tensor-core path (hb_mixed.cu)
+// The tensor-core path runs clusters of MIXED_CLUSTER CTAs; the CTAs of a
+// cluster take consecutive 128-relabelling tiles of the same pair and share
+// every Z-slice tile through TMA multicast.
+constexpr int MIXED_CLUSTER = 4;
+struct WorkItem {
+    int32_t pair;
+    int32_t tile;  // group of MIXED_CLUSTER consecutive 128-relabelling tiles
+};
+struct MixedArgs {
+    const PairMeta *meta;
+    int P;
+    RunOpts o;
+    PairState *st;
+    const ColConst *cc;
+    const uint32_t *bits;
+    const unsigned short *zq;
+    int64_t zq_ld;    // tokens per slice row
+    int64_t zq_rows;  // slice rows
+    const WorkItem *items;
+    int n_work;
+    RecheckItem *list;
+    unsigned int *n_items;
+    unsigned int cap;
+    unsigned int *overflow;
+    unsigned int *timeout;
+    float *T_out;
+    int sms;
+};
+cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
+
 void set_kernel_attributes();
 void set_align_attributes();
 }  // namespace hb

@@ -30,14 +30,46 @@ __global__ void __launch_bounds__(256) k_recheck(const PairMeta *__restrict__ me
         for (int w = threadIdx.x; w < pm.W; w += blockDim.x)
             sm_bits[w] = bits[pm.lab_off + (int64_t)w * pm.B_pad + item.b];
         __syncthreads();
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            i128 acc = 0;
-            for (int i = 0; i < pm.N; ++i) {
-                if ((sm_bits[i >> 5] >> (i & 31)) & 1u)
-                    acc += fixed_from_f32bits(load_f32bits(Z, DT, (pm.z_row + i) * (int64_t)d + j));
+        // exact group-1 sums: up to RC columns per thread per pass; for each
+        // 32-row label word the 32 predicated loads of a column are issued
+        // before any is consumed (loads of unselected rows are skipped)
+        constexpr int RC = 4;
+        for (int j0 = 0; j0 < d; j0 += RC * (int)blockDim.x) {
+            i128 acc[RC];
+#pragma unroll
+            for (int c = 0; c < RC; ++c) acc[c] = 0;
+            for (int w = 0; w < pm.W; ++w) {
+                const uint32_t word = sm_bits[w];
+                if (word == 0u) continue;
+                const unsigned short *rowp16 = nullptr;
+                const uint32_t *rowp32 = nullptr;
+                const int64_t base = (pm.z_row + (int64_t)w * 32) * d;
+                if (DT == DT_F32) rowp32 = reinterpret_cast<const uint32_t *>(Z) + base;
+                else rowp16 = reinterpret_cast<const unsigned short *>(Z) + base;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const int j = j0 + c * (int)blockDim.x + (int)threadIdx.x;
+                    if (j >= d) break;
+                    uint32_t v[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        v[k] = 0u;
+                        if ((word >> k) & 1u)
+                            v[k] = (DT == DT_F32) ? __ldg(rowp32 + (int64_t)k * d + j)
+                                                  : (uint32_t)__ldg(rowp16 + (int64_t)k * d + j) << 16;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) acc[c] += fixed_from_f32bits(v[k]);
+                }
             }
-            s1[j] = fixed_to_f64(acc);
-            s2[j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - acc);
+#pragma unroll
+            for (int c = 0; c < RC; ++c) {
+                const int j = j0 + c * (int)blockDim.x + (int)threadIdx.x;
+                if (j < d) {
+                    s1[j] = fixed_to_f64(acc[c]);
+                    s2[j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - acc[c]);
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0 || threadIdx.x == 32) {

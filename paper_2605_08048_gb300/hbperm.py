@@ -212,3 +212,24 @@ def declared_symbols(header: str | None = None):
     header = header or os.path.join(os.path.dirname(_HERE), "include", "hbperm.h")
     src = open(header).read()
     return sorted(set(re.findall(r"^\s*(?:hb_status|void|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))
+
+
+def set_timing(ctx: Context, enable: bool = True):
+    L = lib()
+    L.hb_ctx_set_timing.argtypes = [C.c_void_p, C.c_int32]
+    L.hb_ctx_set_timing.restype = C.c_int
+    _check(L.hb_ctx_set_timing(ctx.handle, 1 if enable else 0))
+
+
+STAGES = ("align", "zstats_tobs", "labels", "gemm_epilogue", "recheck", "finalize_copy")
+
+
+def stage_times(ctx: Context):
+    """(dict stage -> ms, kernel launches) of the last test call on ctx."""
+    L = lib()
+    L.hb_ctx_stage_times.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
+    L.hb_ctx_stage_times.restype = C.c_int
+    ms = (C.c_float * 6)()
+    nl = C.c_int32(0)
+    _check(L.hb_ctx_stage_times(ctx.handle, ms, C.byref(nl)))
+    return dict(zip(STAGES, [float(v) for v in ms])), int(nl.value)
