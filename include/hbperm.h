@@ -149,6 +149,24 @@ hb_status hb_perm_test_batched(hb_ctx *ctx, int64_t P, const void *XY, const int
 hb_status hb_perm_labels(uint64_t seed, uint32_t stream_id, int64_t n, int64_t N, int64_t b0, int64_t count,
                          uint32_t *bits_out, void *stream);
 
+/* hb_align without any device allocation, for callers that cannot call
+ * cudaMalloc: applications whose device memory is fully reserved by their own
+ * pool allocator, or latency-critical code that cannot take cudaMalloc's
+ * implicit device synchronisation.  (The paper has no counterpart; this is a
+ * deployment variant of hb_align.)  Same arguments, layouts and results as
+ * hb_align, bit for bit, on the current device; no hb_ctx is needed.
+ * All scratch comes from one fixed 2 MiB array in device global memory that
+ * every GPU loading this library holds until the process exits.  Limits:
+ * d <= 1024 and n + m <= 8192, else HB_ERR_UNSUPPORTED with a message in
+ * hb_last_error().  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current), so make it before
+ * any stream capture.  Every call reuses the same array, which keeps the last
+ * call's contents (the call clears what must start at zero); calls that
+ * overlap on the GPU -- from several streams or host threads -- race on it. */
+hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, int64_t m, int64_t d, int32_t dtype,
+                           int32_t align, int32_t reflect_side, void *Z_out, double *u_out, int32_t *skipped,
+                           void *stream);
+
 /* Tracing: per-stage device timing of the calls made on this context, from
  * CUDA events recorded on the caller's stream between the stages (off by
  * default; enabling it adds no synchronisation). */

@@ -653,3 +653,5 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
     if (n_launches) *n_launches = c->last_launches;
     return HB_OK;
 }
+
+void hb_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }

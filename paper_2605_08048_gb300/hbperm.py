@@ -159,6 +159,27 @@ def hb_align(ctx: Context, X: torch.Tensor, Y: torch.Tensor, align=1, reflect_si
     return Z, u, int(sk.value)
 
 
+def hb_align_noalloc(X: torch.Tensor, Y: torch.Tensor, align=1, reflect_side=0, stream=None):
+    """hb_align for callers that cannot allocate device memory: the library
+    takes its scratch from a fixed 2 MiB device array (d <= 1024, n + m <= 8192)
+    instead of a context workspace.  The caller provides the output buffers;
+    here they are allocated by torch only because this is a Python test
+    harness.  Returns (Z, u, skipped)."""
+    L = lib()
+    L.hb_align_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                   C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
+    L.hb_align_noalloc.restype = C.c_int
+    dt = _dtype_code(X)
+    n, d = X.shape
+    m = Y.shape[0]
+    Z = torch.empty((n + m, d), dtype=X.dtype, device=X.device)
+    u = torch.empty(d, dtype=torch.float64, device=X.device)
+    sk = C.c_int32(0)
+    _check(L.hb_align_noalloc(_dev(X), n, _dev(Y), m, d, dt, align, reflect_side, _dev(Z), _dev(u), C.byref(sk),
+                              _stream(stream)))
+    return Z, u, int(sk.value)
+
+
 def hb_perm_test(ctx: Context, X: torch.Tensor, Y: torch.Tensor, opts: hb_opts, want_T=False, stream=None,
                  check=True):
     """Returns (result dict, T_b float32 tensor or None)."""
