@@ -31,13 +31,14 @@ __global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChu
     const void *base = ch.side ? pm.Y : pm.X;
     bool ok = true;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        i128 acc = 0;
+        WinAcc wa;
+        wa.init(4);  // valid inputs satisfy |v| < 2^4
         for (int r = 0; r < ch.nrows; ++r) {
             const uint32_t b = load_f32bits(base, dtype, (int64_t)(ch.row0 + r) * d + j);
             ok &= valid_f32bits(b);
-            acc += fixed_from_f32bits(b);
+            wa.add(b);
         }
-        part[(int64_t)blockIdx.x * d + j] = acc;
+        part[(int64_t)blockIdx.x * d + j] = wa.total();
     }
     if (!ok) atomicOr(bad + ch.pair, 1);
 }
@@ -203,7 +204,6 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
 // ---------------------------------------------------------------------------
 // Z statistics and fixed-point slices, one block (256 threads) per row chunk.
 // ---------------------------------------------------------------------------
-constexpr int ZT = 64;  // columns per tile
 
 // scale exponent E of column j: max |z| < 2^E; q_hi = 2^(E-8)
 __device__ __forceinline__ float qhi_from_max(unsigned int maxbits)
@@ -220,14 +220,27 @@ __device__ __forceinline__ float qhi_from_max(unsigned int maxbits)
 // Integers of magnitude <= 256 are exact in BF16.
 __device__ __forceinline__ void fixed_split(float z, float qh, int S, float &hi, float &lo, float &lo2, float &res)
 {
+    const float ql = qh * (1.0f / 512.0f), ql2 = ql * (1.0f / 512.0f);
+    if (qh <= 1.0f && qh >= 0x1p-100f) {
+        // scaling by the exact reciprocal 2^-k (k >= 0) is exact, as the quotient is
+        const float inv = __int_as_float((254 - ((__float_as_int(qh) >> 23) & 0xff)) << 23);
+        hi = rintf(__fmul_rn(z, inv));
+        const float w = __fsub_rn(z, __fmul_rn(hi, qh));
+        lo = rintf(__fmul_rn(w, inv * 512.0f));
+        res = __fsub_rn(w, __fmul_rn(lo, ql));
+        lo2 = 0.0f;
+        if (S == 3) {
+            lo2 = rintf(__fmul_rn(res, inv * 262144.0f));
+            res = __fsub_rn(res, __fmul_rn(lo2, ql2));
+        }
+        return;
+    }
     hi = rintf(z / qh);
     const float w = __fsub_rn(z, __fmul_rn(hi, qh));
-    const float ql = qh * (1.0f / 512.0f);
     lo = rintf(w / ql);
     res = __fsub_rn(w, __fmul_rn(lo, ql));
     lo2 = 0.0f;
     if (S == 3) {
-        const float ql2 = ql * (1.0f / 512.0f);
         lo2 = rintf(res / ql2);
         res = __fsub_rn(res, __fmul_rn(lo2, ql2));
     }
@@ -239,6 +252,15 @@ __device__ __forceinline__ int64_t slice_row(int j, int s, int S, int cw)
     return (int64_t)(j / cw) * S * cw + (int64_t)s * cw + (j % cw);
 }
 
+// One block (256 threads) per row chunk, tiles of ZS_T columns.  Phase A:
+// thread (column, 16-row part) reads its values (coalesced across columns),
+// adds them exactly to the column totals, splits each once into the
+// fixed-point slices (staged transposed in shared memory) and sums the
+// residuals; phase B stores the slices token-contiguous.
+constexpr int ZS_T = 32;
+constexpr int ZS_PARTS = 256 / ZS_T;               // 8 parts of 16 rows
+constexpr int ZS_ROWS = CHUNK_ROWS / ZS_PARTS;     // 16
+
 template <int DT>
 __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restrict__ meta,
                                                         const RowChunk *__restrict__ chunks, const RunOpts o,
@@ -247,10 +269,9 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
                                                         i128 *__restrict__ tpart, float *__restrict__ cpart,
                                                         unsigned short *__restrict__ zq, int64_t zq_ld)
 {
-    __shared__ float zs[CHUNK_ROWS][ZT + 1];
-    __shared__ float qs[ZT];
-    __shared__ i128 acc_s[4][ZT];
-    __shared__ float cacc_s[4][ZT];
+    __shared__ unsigned short sq[3][ZS_T][CHUNK_ROWS + 2];
+    __shared__ i128 acc_s[ZS_PARTS][ZS_T];
+    __shared__ float cacc_s[ZS_PARTS][ZS_T];
     const RowChunk ch = chunks[blockIdx.x];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
@@ -262,68 +283,54 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
     // the last chunk of the pair also zero-fills the padded tokens of the slices
     const bool last = ch.side == 1 && ch.row0 + ch.nrows == pm.m;
     const int npad = last ? pm.N_pad - pm.N : 0;
+    const int jj = threadIdx.x % ZS_T, part = threadIdx.x / ZS_T;
 
-    for (int j0 = 0; j0 < d; j0 += ZT) {
-        for (int t = threadIdx.x; t < CHUNK_ROWS * ZT; t += blockDim.x) {
-            const int r = t / ZT, jj = t % ZT;
-            float v = 0.0f;
-            if (r < ch.nrows && j0 + jj < d) v = __uint_as_float(load_f32bits(Z, DT, (zrow0 + r) * d + j0 + jj));
-            zs[r][jj] = v;
+    for (int j0 = 0; j0 < d; j0 += ZS_T) {
+        const int j = j0 + jj;
+        const unsigned int mb = j < d ? colmax[(int64_t)ch.pair * o.d_pad + j] : 0u;
+        const float qh = qhi_from_max(mb);
+        WinAcc wa;
+        wa.init(col_bound_exp(mb));
+        float cacc = 0.0f;
+        const int r1 = min(ch.nrows, (part + 1) * ZS_ROWS);
+        for (int r = part * ZS_ROWS; r < r1; ++r) {
+            const uint32_t b = j < d ? load_f32bits(Z, DT, (zrow0 + r) * d + j) : 0u;
+            wa.add(b);
+            const float z = __uint_as_float(b);
+            if (mixed) {
+                float hi, lo, lo2, res;
+                fixed_split(z, qh, S, hi, lo, lo2, res);
+                cacc = __fadd_ru(cacc, fabsf(res));
+                sq[0][jj][r] = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+                sq[1][jj][r] = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+                if (S == 3) sq[2][jj][r] = __bfloat16_as_ushort(__float2bfloat16_rn(lo2));
+            } else {
+                cacc = __fadd_ru(cacc, fabsf(z));
+            }
         }
-        if (threadIdx.x < ZT) {
-            const int j = j0 + threadIdx.x;
-            qs[threadIdx.x] = (mixed && j < d) ? qhi_from_max(colmax[(int64_t)ch.pair * o.d_pad + j]) : 1.0f;
-        }
+        acc_s[part][jj] = wa.total();
+        cacc_s[part][jj] = cacc;
         __syncthreads();
-        // column statistics: 4 threads per column, 32 rows each
-        {
-            const int jj = threadIdx.x % ZT, part = threadIdx.x / ZT;
-            const float qh = qs[jj];
-            i128 acc = 0;
-            float cacc = 0.0f;
-            for (int r = part * 32; r < min(ch.nrows, part * 32 + 32); ++r) {
-                const float z = zs[r][jj];
-                acc += fixed_from_f32bits(__float_as_uint(z));
-                if (mixed) {
-                    float hi, lo, lo2, res;
-                    fixed_split(z, qh, S, hi, lo, lo2, res);
-                    cacc = __fadd_ru(cacc, fabsf(res));
-                } else {
-                    cacc = __fadd_ru(cacc, fabsf(z));
+        if (mixed) {
+            // warp per column, lanes along tokens: token-contiguous stores
+            const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            for (int c = wp; c < ZS_T && j0 + c < d; c += (int)(blockDim.x >> 5)) {
+                for (int s = 0; s < S; ++s) {
+                    unsigned short *dst = zq + slice_row(j0 + c, s, S, o.cw) * zq_ld + pm.z_row;
+                    for (int r = ln; r < ch.nrows; r += 32) dst[tok0 + r] = sq[s][c][r];
+                    for (int k = ln; k < npad; k += 32) dst[pm.N + k] = 0;
                 }
             }
-            acc_s[part][jj] = acc;
-            cacc_s[part][jj] = cacc;
         }
-        // slices, stored token-contiguous (consecutive threads -> consecutive tokens)
-        if (mixed) {
-            for (int t = threadIdx.x; t < ZT * ch.nrows; t += blockDim.x) {
-                const int jj = t / ch.nrows, r = t % ch.nrows;
-                const int j = j0 + jj;
-                if (j >= d) continue;
-                float hi, lo, lo2, res;
-                fixed_split(zs[r][jj], qs[jj], S, hi, lo, lo2, res);
-                const int64_t tok = pm.z_row + tok0 + r;
-                zq[slice_row(j, 0, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-                zq[slice_row(j, 1, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-                if (S == 3) zq[slice_row(j, 2, S, o.cw) * zq_ld + tok] = __bfloat16_as_ushort(__float2bfloat16_rn(lo2));
+        if (threadIdx.x < ZS_T && j0 + threadIdx.x < d) {
+            i128 a = 0;
+            float c = 0.0f;
+            for (int q = 0; q < ZS_PARTS; ++q) {
+                a += acc_s[q][threadIdx.x];
+                c = __fadd_ru(c, cacc_s[q][threadIdx.x]);
             }
-            for (int t = threadIdx.x; t < ZT * npad; t += blockDim.x) {
-                const int jj = t / npad, k = t % npad;
-                const int j = j0 + jj;
-                if (j >= d) continue;
-                const int64_t tok = pm.z_row + pm.N + k;
-                for (int s = 0; s < S; ++s) zq[slice_row(j, s, S, o.cw) * zq_ld + tok] = 0;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < ZT && j0 + threadIdx.x < d) {
-            const int jj = threadIdx.x;
-            const i128 a = acc_s[0][jj] + acc_s[1][jj] + acc_s[2][jj] + acc_s[3][jj];
-            const float c =
-                __fadd_ru(__fadd_ru(cacc_s[0][jj], cacc_s[1][jj]), __fadd_ru(cacc_s[2][jj], cacc_s[3][jj]));
-            tpart[(int64_t)blockIdx.x * d + j0 + jj] = a;
-            cpart[(int64_t)blockIdx.x * d + j0 + jj] = c;
+            tpart[(int64_t)blockIdx.x * d + j0 + threadIdx.x] = a;
+            cpart[(int64_t)blockIdx.x * d + j0 + threadIdx.x] = c;
         }
         __syncthreads();
     }

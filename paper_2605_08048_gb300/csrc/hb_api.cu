@@ -67,6 +67,10 @@ struct hb_ctx {
     cudaEvent_t tev[7] = {};
     float last_ms[6] = {};
     int last_launches = 0;
+    // side stream for the label draws, which depend on no data and overlap
+    // the alignment stages (fork/join with events on the caller's stream)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 static void mark(hb_ctx *c, int k, cudaStream_t s)
@@ -84,7 +88,10 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
     hb_ctx *c = new hb_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return fail(HB_ERR_CUDA, "cudaEventCreate failed");
     }
@@ -103,6 +110,12 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
     }
     for (int k = 0; k < 7; ++k)
         if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFreeHost(c->stage);
     delete c;
@@ -371,7 +384,9 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         (int64_t)1 << 30, (mixed ? pl.total_B / 256 : pl.total_B / 16) + 4096);
 
     for (int attempt = 0; attempt < 3; ++attempt) {
-        const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 4 * c->sms));
+        // recheck batch: items whose exact sums share the scratch at once (<= 256 MB of FP64)
+        const int rgrid = (int)std::max<int64_t>(
+            1, std::min<int64_t>(cap, (int64_t)(256u << 20) / (int64_t)(2 * sizeof(double) * pl.o.d)));
         Bufs b{};
         Carve plan_cv(nullptr);
         const size_t need = carve(plan_cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid);
@@ -406,7 +421,14 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             CK(cudaMemcpyAsync(b.items, hs_ + mbytes + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, s));
         }
         CK(cudaEventRecord(c->stage_done, s));
-        if (mixed || o.path == HB_PATH_MIXED) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
+        if (!align_only) {
+            // labels on the side stream from here on, concurrently with steps 1-4
+            CK(cudaEventRecord(c->fork, s));
+            CK(cudaStreamWaitEvent(c->side, c->fork, 0));
+            launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, c->side);
+            CK(cudaEventRecord(c->join, c->side));
+        }
+        if (!align_only) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
         if (!align_only) CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
         if (mixed && o.d_pad != d)
             CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
@@ -416,7 +438,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         mark(c, 0, s);
         launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
         launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
-        unsigned int *colmax = (o.path == HB_PATH_MIXED) ? b.colmax : nullptr;
+        unsigned int *colmax = align_only ? nullptr : b.colmax;  // column maxima: slice scales and exact-sum windows
         launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, colmax, s);
         CK(cudaGetLastError());
 
@@ -443,7 +465,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
 
         // step 5: labels, group sums + statistic + band, exact recheck
         mark(c, 2, s);
-        launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, s);
+        CK(cudaStreamWaitEvent(s, c->join, 0));  // the "labels" stage is the part not hidden
         mark(c, 3, s);
         CK(cudaGetLastError());
         if (mixed) {
@@ -479,8 +501,8 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         }
         CK(cudaGetLastError());
         mark(c, 4, s);
-        launch_recheck(rgrid, sizeof(uint32_t) * pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.bits, b.list, b.counters,
-                       cap, b.scratch, T_out, s);
+        launch_recheck(cap, (unsigned int)rgrid, pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.colmax, b.bits, b.list,
+                       b.counters, b.scratch, T_out, s);
         mark(c, 5, s);
         launch_finalize(b.meta, P, o, b.st, b.out, s);
         CK(cudaGetLastError());
@@ -505,7 +527,9 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], c->tev[k], c->tev[k + 1]);
         }
         // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck + finalize
-        c->last_launches = 10 + (int)((P + 65534) / 65535) * (mixed ? 1 : 2);
+        // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck (2 per batch) + finalize
+        const int pchunks = (int)((P + 65534) / 65535);
+        c->last_launches = 8 + pchunks + (mixed ? 1 : pchunks) + 2 * (int)((cap + rgrid - 1) / rgrid);
         return HB_OK;
     }
     return fail(HB_ERR_CUDA, "recheck list kept overflowing");

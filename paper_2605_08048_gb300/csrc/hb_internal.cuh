@@ -118,6 +118,60 @@ __device__ __forceinline__ i128 fixed_from_f32bits(uint32_t b)
     return (b >> 31) ? -(i128)m : (i128)m;
 }
 
+// Exact sums on the same 2^-87 grid, cheaper: values within 55 binades below
+// a column bound 2^E are accumulated as integers of unit 2^(E-55) in 64 bits
+// (at most 2^55 each, so 128 of them cannot overflow); the rare smaller values
+// go through the 128-bit path.  Flushing below 2^-64 is unchanged.
+struct WinAcc {
+    int64_t acc;
+    i128 slow;
+    int eb;    // biased FP32 exponent of the window: E + 95 (256 = no window)
+    int sh;    // shift from the window unit to the 2^-87 grid: E + 32
+    __device__ __forceinline__ void init(int E)
+    {
+        acc = 0;
+        slow = 0;
+        if (E + 32 >= 0 && E <= 120) {
+            eb = E + 95;
+            sh = E + 32;
+        } else {
+            eb = 256;
+            sh = 0;
+        }
+    }
+    __device__ __forceinline__ void add(uint32_t b)
+    {
+        const int e = (int)((b >> 23) & 0xffu);
+        if (e < 63) return;  // |v| < 2^-64 counts as 0
+        const int s = e - eb;
+        if (s >= 0) {
+            const int64_t v = (int64_t)((b & 0x7fffffu) | 0x800000u) << s;
+            acc += (b >> 31) ? -v : v;
+        } else {
+            slow += fixed_from_f32bits(b);
+        }
+    }
+    // moves the 64-bit part into the 128-bit total (call at least every 128 adds)
+    __device__ __forceinline__ void flush()
+    {
+        slow += (i128)acc << sh;
+        acc = 0;
+    }
+    __device__ __forceinline__ i128 total()
+    {
+        flush();
+        return slow;
+    }
+};
+
+// E with |v| < 2^E for every value of a column whose maximum magnitude has
+// FP32 bit pattern maxbits (0 for an all-zero column).
+__device__ __forceinline__ int col_bound_exp(unsigned int maxbits)
+{
+    if (maxbits == 0u) return -200;
+    return (int)((maxbits >> 23) & 0xffu) - 126;
+}
+
 __device__ __forceinline__ double pow2d(int e)  // 2^e for -1022 <= e <= 1023
 {
     return __longlong_as_double((long long)(e + 1023) << 52);

@@ -27,9 +27,10 @@ void launch_labels_pipeline(const PairMeta *meta, const PairState *pst, int P, i
 void launch_plain(const PairMeta *meta, int P, int max_Bpad, const RunOpts &o, PairState *pst, const void *Z,
                   const ColConst *cc, const uint32_t *bits, RecheckItem *list, unsigned int *n_items,
                   unsigned int cap, unsigned int *overflow, float *T_out, cudaStream_t st);
-void launch_recheck(int grid, size_t smem, const PairMeta *meta, const RunOpts &o, PairState *pst, const void *Z,
-                    const i128 *t_ex, const uint32_t *bits, const RecheckItem *list, const unsigned int *n_items,
-                    unsigned int cap, double *scratch, float *T_out, cudaStream_t st);
+void launch_recheck(unsigned int cap, unsigned int batch, int max_W, const PairMeta *meta, const RunOpts &o,
+                    PairState *pst, const void *Z, const i128 *t_ex, const unsigned int *colmax, const uint32_t *bits,
+                    const RecheckItem *list, const unsigned int *n_items, double *sums, float *T_out,
+                    cudaStream_t st);
 void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairState *pst, PairOut *out,
                      cudaStream_t st);
 // tensor-core path (hb_mixed.cu)

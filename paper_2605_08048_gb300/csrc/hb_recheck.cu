@@ -11,85 +11,89 @@
 
 namespace hb {
 
+// Stage 1: exact group sums of a batch of rechecked relabellings.  Block
+// (item, 256-column slice); each thread owns one column and, per 32-row label
+// word, issues the loads of the selected rows before consuming any.
 template <int DT>
-__global__ void __launch_bounds__(256) k_recheck(const PairMeta *__restrict__ meta, const RunOpts o,
-                                                 PairState *__restrict__ st, const void *__restrict__ Z,
-                                                 const i128 *__restrict__ t_ex, const uint32_t *__restrict__ bits,
-                                                 const RecheckItem *__restrict__ list,
-                                                 const unsigned int *__restrict__ n_items, unsigned int cap,
-                                                 double *__restrict__ scratch, float *__restrict__ T_out)
+__global__ void __launch_bounds__(256) k_recheck_sums(const PairMeta *__restrict__ meta, const RunOpts o,
+                                                      const void *__restrict__ Z, const i128 *__restrict__ t_ex,
+                                                      const unsigned int *__restrict__ colmax,
+                                                      const uint32_t *__restrict__ bits,
+                                                      const RecheckItem *__restrict__ list,
+                                                      const unsigned int *__restrict__ n_items, unsigned int cap,
+                                                      unsigned int batch0, double *__restrict__ sums)
 {
     extern __shared__ uint32_t sm_bits[];
-    __shared__ double q[2];
-    const int d = o.d;
     const unsigned int total = min(*n_items, cap);
-    double *s1 = scratch + (int64_t)blockIdx.x * 2 * d, *s2 = s1 + d;
-    for (unsigned int it = blockIdx.x; it < total; it += gridDim.x) {
-        const RecheckItem item = list[it];
-        const PairMeta pm = meta[item.pair];
-        for (int w = threadIdx.x; w < pm.W; w += blockDim.x)
-            sm_bits[w] = bits[pm.lab_off + (int64_t)w * pm.B_pad + item.b];
-        __syncthreads();
-        // exact group-1 sums: up to RC columns per thread per pass; for each
-        // 32-row label word the 32 predicated loads of a column are issued
-        // before any is consumed (loads of unselected rows are skipped)
-        constexpr int RC = 4;
-        for (int j0 = 0; j0 < d; j0 += RC * (int)blockDim.x) {
-            i128 acc[RC];
+    const unsigned int it = batch0 + blockIdx.x;
+    if (it >= total) return;
+    const int d = o.d;
+    const RecheckItem item = list[it];
+    const PairMeta pm = meta[item.pair];
+    for (int w = threadIdx.x; w < pm.W; w += blockDim.x) sm_bits[w] = bits[pm.lab_off + (int64_t)w * pm.B_pad + item.b];
+    __syncthreads();
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    WinAcc wa;
+    wa.init(col_bound_exp(colmax[(int64_t)item.pair * o.d_pad + j]));
+    for (int w = 0; w < pm.W; ++w) {
+        const uint32_t word = sm_bits[w];
+        if (word == 0u) continue;
+        const int64_t base = (pm.z_row + (int64_t)w * 32) * d + j;
+        // two halves of 16 rows: their loads are issued before any is consumed
 #pragma unroll
-            for (int c = 0; c < RC; ++c) acc[c] = 0;
-            for (int w = 0; w < pm.W; ++w) {
-                const uint32_t word = sm_bits[w];
-                if (word == 0u) continue;
-                const unsigned short *rowp16 = nullptr;
-                const uint32_t *rowp32 = nullptr;
-                const int64_t base = (pm.z_row + (int64_t)w * 32) * d;
-                if (DT == DT_F32) rowp32 = reinterpret_cast<const uint32_t *>(Z) + base;
-                else rowp16 = reinterpret_cast<const unsigned short *>(Z) + base;
+        for (int h = 0; h < 2; ++h) {
+            uint32_t v[16];
 #pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    const int j = j0 + c * (int)blockDim.x + (int)threadIdx.x;
-                    if (j >= d) break;
-                    uint32_t v[32];
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        v[k] = 0u;
-                        if ((word >> k) & 1u)
-                            v[k] = (DT == DT_F32) ? __ldg(rowp32 + (int64_t)k * d + j)
-                                                  : (uint32_t)__ldg(rowp16 + (int64_t)k * d + j) << 16;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) acc[c] += fixed_from_f32bits(v[k]);
-                }
+            for (int k = 0; k < 16; ++k) {
+                const int kk = 16 * h + k;
+                v[k] = 0u;
+                if ((word >> kk) & 1u)
+                    v[k] = (DT == DT_F32) ? __ldg(reinterpret_cast<const uint32_t *>(Z) + base + (int64_t)kk * d)
+                                          : (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(Z) + base +
+                                                            (int64_t)kk * d)
+                                                << 16;
             }
 #pragma unroll
-            for (int c = 0; c < RC; ++c) {
-                const int j = j0 + c * (int)blockDim.x + (int)threadIdx.x;
-                if (j < d) {
-                    s1[j] = fixed_to_f64(acc[c]);
-                    s2[j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - acc[c]);
-                }
-            }
+            for (int k = 0; k < 16; ++k) wa.add(v[k]);
         }
-        __syncthreads();
-        if (threadIdx.x == 0 || threadIdx.x == 32) {
-            const double *v = threadIdx.x ? s2 : s1;
-            double a = 0.0;
-            for (int j = 0; j < d; ++j) a = __fma_rn(v[j], v[j], a);
-            q[threadIdx.x ? 1 : 0] = a;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const PairState s = st[item.pair];
-            const double A1 = group_value_f64(o.stat, q[0], (double)pm.n, (double)d);
-            const double A2 = group_value_f64(o.stat, q[1], (double)pm.m, (double)d);
-            const int e = exceeds_f64(o.stat, o.alt, A1, A2, s.A1o, s.A2o);
-            if (e) atomicAdd(&st[item.pair].count, 1ull);
-            atomicAdd(&st[item.pair].rechecked, 1ull);
-            if (T_out && pm.T_off >= 0) T_out[pm.T_off + item.b] = (float)stat_T_f64(o.stat, A1, A2);
-        }
-        __syncthreads();
+        wa.flush();
     }
+    const i128 acc = wa.total();
+    double *out = sums + (int64_t)blockIdx.x * 2 * d;
+    out[j] = fixed_to_f64(acc);
+    out[d + j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - acc);
+}
+
+// Stage 2: squared norms as sequential FMA chains over j = 0..d-1 (two
+// threads per item, one per group, all items in flight together), then the
+// exact decision with correctly rounded IEEE operations only.
+__global__ void k_recheck_decide(const PairMeta *__restrict__ meta, const RunOpts o, PairState *__restrict__ st,
+                                 const RecheckItem *__restrict__ list, const unsigned int *__restrict__ n_items,
+                                 unsigned int cap, unsigned int batch0, unsigned int batch,
+                                 const double *__restrict__ sums, float *__restrict__ T_out)
+{
+    const unsigned int total = min(*n_items, cap);
+    const unsigned int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int k = t >> 1, g = t & 1u;
+    const unsigned int it = batch0 + k;
+    const bool live = k < batch && it < total;
+    const int d = o.d;
+    double q = 0.0;
+    if (live) {
+        const double *v = sums + (int64_t)k * 2 * d + (int64_t)g * d;
+        for (int j = 0; j < d; ++j) q = __fma_rn(v[j], v[j], q);
+    }
+    const double q2 = __shfl_down_sync(0xffffffffu, q, 1);
+    if (!live || g != 0u) return;
+    const RecheckItem item = list[it];
+    const PairMeta pm = meta[item.pair];
+    const PairState s = st[item.pair];
+    const double A1 = group_value_f64(o.stat, q, (double)pm.n, (double)d);
+    const double A2 = group_value_f64(o.stat, q2, (double)pm.m, (double)d);
+    if (exceeds_f64(o.stat, o.alt, A1, A2, s.A1o, s.A2o)) atomicAdd(&st[item.pair].count, 1ull);
+    atomicAdd(&st[item.pair].rechecked, 1ull);
+    if (T_out && pm.T_off >= 0) T_out[pm.T_off + item.b] = (float)stat_T_f64(o.stat, A1, A2);
 }
 
 // p = (1 + count)/(B + 1), or count/C(N, n) when every split is enumerated.
@@ -121,14 +125,24 @@ __global__ void k_finalize(const PairMeta *__restrict__ meta, int P, const RunOp
     out[p] = r;
 }
 
-void launch_recheck(int grid, size_t smem, const PairMeta *meta, const RunOpts &o, PairState *pst, const void *Z,
-                    const i128 *t_ex, const uint32_t *bits, const RecheckItem *list, const unsigned int *n_items,
-                    unsigned int cap, double *scratch, float *T_out, cudaStream_t st)
+void launch_recheck(unsigned int cap, unsigned int batch, int max_W, const PairMeta *meta, const RunOpts &o,
+                    PairState *pst, const void *Z, const i128 *t_ex, const unsigned int *colmax, const uint32_t *bits,
+                    const RecheckItem *list, const unsigned int *n_items, double *sums, float *T_out,
+                    cudaStream_t st)
 {
-    if (o.dtype == DT_F32)
-        k_recheck<DT_F32><<<grid, 256, smem, st>>>(meta, o, pst, Z, t_ex, bits, list, n_items, cap, scratch, T_out);
-    else
-        k_recheck<DT_BF16><<<grid, 256, smem, st>>>(meta, o, pst, Z, t_ex, bits, list, n_items, cap, scratch, T_out);
+    // batches up to the list capacity; batches past the actual count exit at once
+    const size_t smem = sizeof(uint32_t) * (size_t)max_W;
+    const dim3 g1(batch, (unsigned)((o.d + 255) / 256));
+    for (unsigned int b0 = 0; b0 < cap; b0 += batch) {
+        if (o.dtype == DT_F32)
+            k_recheck_sums<DT_F32><<<g1, 256, smem, st>>>(meta, o, Z, t_ex, colmax, bits, list, n_items, cap, b0,
+                                                          sums);
+        else
+            k_recheck_sums<DT_BF16><<<g1, 256, smem, st>>>(meta, o, Z, t_ex, colmax, bits, list, n_items, cap, b0,
+                                                           sums);
+        k_recheck_decide<<<(2 * batch + 127) / 128, 128, 0, st>>>(meta, o, pst, list, n_items, cap, b0, batch, sums,
+                                                                 T_out);
+    }
 }
 
 void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairState *pst, PairOut *out,
@@ -140,8 +154,8 @@ void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairSt
 void set_kernel_attributes()
 {
     const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_recheck<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_recheck<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_recheck_sums<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_recheck_sums<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     set_align_attributes();
 }
 
