@@ -167,6 +167,67 @@ hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, int64_t m, i
                            int32_t align, int32_t reflect_side, void *Z_out, double *u_out, int32_t *skipped,
                            void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned triage.  A component of this library's batched workflow; the paper
+ * has no learned part.  A network predicts, from cheap per-pair features,
+ * quantiles of the null distribution of |T| that the full test (Eq. pvalue)
+ * would draw; pairs whose predicted p is clearly outside a band around alpha
+ * skip the full test.
+ * ------------------------------------------------------------------------- */
+#define HB_TRIAGE_NFEAT 19
+#define HB_TRIAGE_NQ 9
+
+/* Features of P pairs (packed as for hb_perm_test_batched; XY device):
+ * log n, log m, log(d * lambda_k) for the 16 Ritz values lambda_k of the
+ * pooled scatter Z^T Z / N of the aligned pair (Sec. 3.1) after 4 block
+ * subspace iterations V <- orth(Z^T Z V / N) from a fixed Philox start block
+ * (any orthonormal basis of the iterate's span gives the same Ritz values),
+ * and 10 * T_obs.  Runs the alignment and T_obs only (no relabellings).
+ * feat_out: device [P][19]; tobs_out: device [P] FP64, nullable; out: host [P]
+ * (status, T_obs, r_x, r_y).  Needs d <= 1024. */
+hb_status hb_triage_features(hb_ctx *ctx, int64_t P, const void *XY, const int64_t *n, const int64_t *m, int64_t d,
+                             int32_t dtype, const hb_opts *opts, float *feat_out, double *tobs_out, hb_result *out,
+                             void *stream);
+
+/* Training targets from the method's own relabellings: runs the full test of
+ * P pairs exactly as hb_perm_test_batched and writes, per pair, the empirical
+ * quantiles of |T_b| (b = 0..B-1; the ceil(level * B)-th smallest) at levels
+ * 0.5, 0.8, 0.9, 0.95, 0.975, 0.99, 0.995, 0.998, 0.999, times 100, into
+ * quant_out (device [P][9]).  out: host [P].  Needs B <= 32768. */
+hb_status hb_null_quantiles(hb_ctx *ctx, int64_t P, const void *XY, const int64_t *n, const int64_t *m, int64_t d,
+                            int32_t dtype, const hb_opts *opts, float *quant_out, hb_result *out, void *stream);
+
+/* The triage network 19 -> 256 (ReLU) -> 256 (ReLU) -> 9.  Parameters form one
+ * flat FP32 vector [W1 19x256 | b1 256 | W2 256x256 | b2 256 | W3 256x9 | b3 9]
+ * (weights input-major, row-major); the forward uses the weights rounded to
+ * BF16 (params_bf16, same layout) with FP32 accumulation.  All pointers are
+ * device memory owned by the caller, each hb_mlp_param_count() long. */
+typedef struct {
+    float *params;
+    uint16_t *params_bf16;
+    float *grad;
+    float *adam_m;
+    float *adam_v;
+} hb_mlp;
+
+int64_t hb_mlp_param_count(void);
+/* params_bf16 <- BF16(params) */
+hb_status hb_mlp_sync(const hb_mlp *net, void *stream);
+/* out (device [P][9]) <- network(feat (device [P][19])) */
+hb_status hb_mlp_forward(hb_ctx *ctx, const hb_mlp *net, int64_t P, const float *feat, float *out, void *stream);
+/* net->grad <- gradient of the mean pinball loss of network(feat) against
+ * target (device [P][9]; levels as hb_null_quantiles); loss (device, 1 float). */
+hb_status hb_mlp_grad(hb_ctx *ctx, const hb_mlp *net, int64_t P, const float *feat, const float *target, float *loss,
+                      void *stream);
+/* One Adam step (Kingma and Ba, 2015; beta 0.9/0.999, eps 1e-8) at step t >= 1
+ * on params with net->grad, updating the moments and params_bf16. */
+hb_status hb_mlp_adam(const hb_mlp *net, float lr, int64_t t, void *stream);
+/* Predicted p of P pairs from predicted quantiles (x100, device [P][9], made
+ * non-decreasing) and T_obs (device [P]): 1 - F(|T_obs|), F linear between
+ * (q_k, level_k), from (0, 0) below q_1, the last slope continued above q_9
+ * and floored at p = 1e-4.  p_out: device [P]. */
+hb_status hb_triage_predict_p(int64_t P, const float *quant, const double *tobs, float *p_out, void *stream);
+
 /* Tracing: per-stage device timing of the calls made on this context, from
  * CUDA events recorded on the caller's stream between the stages (off by
  * default; enabling it adds no synchronisation). */

@@ -71,6 +71,9 @@ struct hb_ctx {
     // the alignment stages (fork/join with events on the caller's stream)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // relabelling statistics of hb_null_quantiles
+    void *tbuf = nullptr;
+    size_t tbuf_cap = 0;
 };
 
 static void mark(hb_ctx *c, int k, cudaStream_t s)
@@ -116,6 +119,7 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
     }
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
+    if (c->tbuf) cudaFree(c->tbuf);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFreeHost(c->stage);
     delete c;
@@ -331,6 +335,7 @@ struct Bufs {
     PairOut *out;
     void *xy;
     WorkItem *items;
+    float *lam;  // Ritz values [P][16] (features mode)
 };
 
 static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool own_Z, size_t xy_bytes,
@@ -364,16 +369,25 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
         b.scratch = cv.take<double>((size_t)rgrid * 2 * d);
         b.out = cv.take<PairOut>(P);
         b.items = pl.o.path == HB_PATH_MIXED ? cv.take<WorkItem>(pl.items.size()) : nullptr;
+        b.lam = cv.take<float>((size_t)P * 16);
     }
     return cv.off;
 }
 
 
 // The whole launch sequence.  Xp/Yp: device pointers per pair.
+// Optional outputs of the triage entry points.
+struct TriageOut {
+    float *feat = nullptr;   // features mode: steps 1-4 only, then [P][19] features
+    double *tobs = nullptr;  // features mode: T_obs per pair
+    float *quant = nullptr;  // null-quantile mode: [P][9] quantiles of |T_b| (x100), T_out required
+};
+
 static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
                      bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
-                     cudaStream_t s, std::vector<PairOut> &out)
+                     cudaStream_t s, std::vector<PairOut> &out, const TriageOut *tri = nullptr)
 {
+    const bool features = tri && tri->feat;
     set_attrs(c);
     const int P = pl.P;
     const RunOpts o = pl.o;
@@ -421,7 +435,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             CK(cudaMemcpyAsync(b.items, hs_ + mbytes + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, s));
         }
         CK(cudaEventRecord(c->stage_done, s));
-        if (!align_only) {
+        if (!align_only && !features) {
             // labels on the side stream from here on, concurrently with steps 1-4
             CK(cudaEventRecord(c->fork, s));
             CK(cudaStreamWaitEvent(c->side, c->fork, 0));
@@ -463,6 +477,12 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
         CK(cudaGetLastError());
 
+        if (features) {
+            mark(c, 2, s);
+            mark(c, 3, s);
+            launch_features(b.meta, P, o, b.st, Z, b.lam, tri->feat, tri->tobs, s);
+            mark(c, 4, s);
+        } else {
         // step 5: labels, group sums + statistic + band, exact recheck
         mark(c, 2, s);
         CK(cudaStreamWaitEvent(s, c->join, 0));  // the "labels" stage is the part not hidden
@@ -503,8 +523,14 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         mark(c, 4, s);
         launch_recheck(cap, (unsigned int)rgrid, pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.colmax, b.bits, b.list,
                        b.counters, b.scratch, T_out, s);
+        }
         mark(c, 5, s);
         launch_finalize(b.meta, P, o, b.st, b.out, s);
+        if (tri && tri->quant) {
+            int64_t maxB = 1;
+            for (int p = 0; p < P; ++p) maxB = std::max<int64_t>(maxB, pl.meta[p].B);
+            launch_null_quantiles(b.meta, P, (int)maxB, T_out, b.st, 100.0f, tri->quant, s);
+        }
         CK(cudaGetLastError());
 
         // one copy back: results and the counters
@@ -526,7 +552,6 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         if (c->timing) {
             for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], c->tev[k], c->tev[k + 1]);
         }
-        // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck + finalize
         // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck (2 per batch) + finalize
         const int pchunks = (int)((P + 65534) / 65535);
         c->last_launches = 8 + pchunks + (mixed ? 1 : pchunks) + 2 * (int)((cap + rgrid - 1) / rgrid);
@@ -679,3 +704,138 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
 }
 
 void hb_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
+
+// ---------------------------------------------------------------------------
+// learned triage
+// ---------------------------------------------------------------------------
+static hb_status batched_common(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m, int64_t d,
+                                int32_t dtype, const hb_opts *opts, hb_result *res, float *T_out,
+                                const TriageOut *tri, bool features, void *stream)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    if (P < 1 || P > (1 << 24)) return fail(HB_ERR_INVALID_ARG, "P = %lld", (long long)P);
+    if (!XY || !n || !m || !res) return fail(HB_ERR_INVALID_ARG, "XY, n, m and out must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    CK(cudaSetDevice(c->device));
+    hb_opts op = *opts;
+    if (features) {
+        op.path = HB_PATH_FP32_PLAIN;  // no slices needed
+        op.B = 1;
+        op.exhaustive = 0;
+    }
+    Plan pl;
+    hs = make_plan(pl, P, n, m, d, dtype, op, false, T_out != nullptr);
+    if (hs != HB_OK) return hs;
+    const size_t esz = dtype == HB_F32 ? 4 : 2;
+    int64_t off = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        pl.meta[p].X = (const char *)XY + (size_t)off * d * esz;
+        pl.meta[p].Y = (const char *)pl.meta[p].X + (size_t)n[p] * d * esz;
+        off += n[p] + m[p];
+    }
+    std::vector<PairOut> out;
+    hs = run(c, pl, nullptr, 0, nullptr, false, nullptr, nullptr, nullptr, T_out, (cudaStream_t)stream, out, tri);
+    if (hs != HB_OK) return hs;
+    for (int64_t p = 0; p < P; ++p) fill_result(out[p], &res[p]);
+    g_err.clear();
+    return HB_OK;
+}
+
+extern "C" hb_status hb_triage_features(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m,
+                                        int64_t d, int32_t dtype, const hb_opts *opts, float *feat_out,
+                                        double *tobs_out, hb_result *out, void *stream)
+{
+    if (!feat_out) return fail(HB_ERR_INVALID_ARG, "feat_out is NULL");
+    if (d > 1024) return fail(HB_ERR_UNSUPPORTED, "triage features need d <= 1024");
+    TriageOut tri;
+    tri.feat = feat_out;
+    tri.tobs = tobs_out;
+    return batched_common(c, P, XY, n, m, d, dtype, opts, out, nullptr, &tri, true, stream);
+}
+
+extern "C" hb_status hb_null_quantiles(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m,
+                                       int64_t d, int32_t dtype, const hb_opts *opts, float *quant_out,
+                                       hb_result *out, void *stream)
+{
+    if (!c || !quant_out || !opts) return fail(HB_ERR_INVALID_ARG, "ctx, opts and quant_out must be non-NULL");
+    if (P < 1) return fail(HB_ERR_INVALID_ARG, "P = %lld", (long long)P);
+    if (opts->exhaustive || opts->B > 32768) return fail(HB_ERR_UNSUPPORTED, "null quantiles need B <= 32768");
+    const size_t need = sizeof(float) * (size_t)P * (size_t)std::max<int64_t>(1, opts->B);
+    if (need > c->tbuf_cap) {
+        if (c->tbuf) cudaFree(c->tbuf);
+        c->tbuf = nullptr;
+        c->tbuf_cap = 0;
+        if (cudaMalloc(&c->tbuf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HB_ERR_OOM, "T buffer of %zu bytes could not be allocated", need);
+        }
+        c->tbuf_cap = need;
+    }
+    TriageOut tri;
+    tri.quant = quant_out;
+    return batched_common(c, P, XY, n, m, d, dtype, opts, out, (float *)c->tbuf, &tri, false, stream);
+}
+
+extern "C" int64_t hb_mlp_param_count(void) { return mlp_param_count(); }
+
+static bool mlp_ok(const hb_mlp *net)
+{
+    return net && net->params && net->params_bf16 && net->grad && net->adam_m && net->adam_v;
+}
+
+extern "C" hb_status hb_mlp_sync(const hb_mlp *net, void *stream)
+{
+    if (!net || !net->params || !net->params_bf16) return fail(HB_ERR_INVALID_ARG, "net is incomplete");
+    mlp_to_bf16(net->params, net->params_bf16, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mlp_forward(hb_ctx *c, const hb_mlp *net, int64_t P, const float *feat, float *out,
+                                    void *stream)
+{
+    if (!c || !net || !net->params || !net->params_bf16 || !feat || !out || P < 1 || P > (1 << 22))
+        return fail(HB_ERR_INVALID_ARG, "bad hb_mlp_forward arguments");
+    CK(cudaSetDevice(c->device));
+    hb_status hs = ensure_ws(c, sizeof(float) * (size_t)mlp_work_floats((int)P));
+    if (hs != HB_OK) return hs;
+    mlp_forward(net->params, net->params_bf16, (int)P, feat, (float *)c->ws, out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mlp_grad(hb_ctx *c, const hb_mlp *net, int64_t P, const float *feat, const float *target,
+                                 float *loss, void *stream)
+{
+    if (!c || !mlp_ok(net) || !feat || !target || !loss || P < 1 || P > (1 << 22))
+        return fail(HB_ERR_INVALID_ARG, "bad hb_mlp_grad arguments");
+    CK(cudaSetDevice(c->device));
+    hb_status hs = ensure_ws(c, sizeof(float) * (size_t)mlp_work_floats((int)P));
+    if (hs != HB_OK) return hs;
+    float *work = (float *)c->ws;
+    float *y = work + (int64_t)P * 256 * 4;  // after a1, h1, a2, h2
+    mlp_forward(net->params, net->params_bf16, (int)P, feat, work, y, (cudaStream_t)stream);
+    mlp_backward(net->params, net->params_bf16, (int)P, feat, target, work, net->grad, loss, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mlp_adam(const hb_mlp *net, float lr, int64_t t, void *stream)
+{
+    if (!mlp_ok(net) || t < 1) return fail(HB_ERR_INVALID_ARG, "bad hb_mlp_adam arguments");
+    mlp_adam(net->params, net->params_bf16, net->grad, net->adam_m, net->adam_v, lr, t, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" hb_status hb_triage_predict_p(int64_t P, const float *quant, const double *tobs, float *p_out,
+                                         void *stream)
+{
+    if (P < 1 || !quant || !tobs || !p_out) return fail(HB_ERR_INVALID_ARG, "bad hb_triage_predict_p arguments");
+    launch_predict_p((int)P, quant, 100.0f, tobs, p_out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return HB_OK;
+}

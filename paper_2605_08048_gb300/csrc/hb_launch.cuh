@@ -64,6 +64,22 @@ struct MixedArgs {
 };
 cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
 
+// learned triage (hb_triage.cu)
+void launch_features(const PairMeta *meta, int P, const RunOpts &o, const PairState *st, const void *Z, float *lam,
+                     float *feat, double *tobs, cudaStream_t s);
+void launch_null_quantiles(const PairMeta *meta, int P, int max_B, const float *T, const PairState *st, float scale,
+                           float *q_out, cudaStream_t s);
+int64_t mlp_param_count();
+int64_t mlp_work_floats(int P);
+void mlp_forward(const float *params, const unsigned short *wh, int P, const float *feat, float *work, float *y_out,
+                 cudaStream_t s);
+void mlp_backward(const float *params, const unsigned short *wh, int P, const float *feat, const float *target,
+                  float *work, float *grad, float *loss, cudaStream_t s);
+void mlp_adam(float *params, unsigned short *wh, const float *grad, float *m, float *v, float lr, int64_t t,
+              cudaStream_t s);
+void mlp_to_bf16(const float *params, unsigned short *wh, cudaStream_t s);
+void launch_predict_p(int P, const float *q_scaled, float scale, const double *tobs, float *p_out, cudaStream_t s);
+
 void set_kernel_attributes();
 void set_align_attributes();
 }  // namespace hb

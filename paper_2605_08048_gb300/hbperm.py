@@ -232,7 +232,7 @@ def declared_symbols(header: str | None = None):
     import re
     header = header or os.path.join(os.path.dirname(_HERE), "include", "hbperm.h")
     src = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:hb_status|void|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:hb_status|void|int64_t|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))
 
 
 def set_timing(ctx: Context, enable: bool = True):
@@ -254,3 +254,114 @@ def stage_times(ctx: Context):
     nl = C.c_int32(0)
     _check(L.hb_ctx_stage_times(ctx.handle, ms, C.byref(nl)))
     return dict(zip(STAGES, [float(v) for v in ms])), int(nl.value)
+
+
+# --------------------------------------------------------------------------
+# learned triage
+# --------------------------------------------------------------------------
+TRIAGE_NFEAT, TRIAGE_NQ = 19, 9
+TRIAGE_LEVELS = (0.5, 0.8, 0.9, 0.95, 0.975, 0.99, 0.995, 0.998, 0.999)
+
+
+class hb_mlp(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("params_bf16", C.c_void_p), ("grad", C.c_void_p), ("adam_m", C.c_void_p),
+                ("adam_v", C.c_void_p)]
+
+
+def _batched_args(XY, n, m):
+    P = len(n)
+    return P, (C.c_int64 * P)(*[int(v) for v in n]), (C.c_int64 * P)(*[int(v) for v in m])
+
+
+def triage_features(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, stream=None):
+    """(features [P][19] float32, T_obs [P] float64, results) of packed pairs."""
+    L = lib()
+    vp = C.c_void_p
+    L.hb_triage_features.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_int64, C.c_int32, C.POINTER(hb_opts), vp, vp,
+                                     C.POINTER(hb_result), vp]
+    L.hb_triage_features.restype = C.c_int
+    P, na, ma = _batched_args(XY, n, m)
+    feat = torch.empty((P, TRIAGE_NFEAT), dtype=torch.float32, device=XY.device)
+    tobs = torch.empty(P, dtype=torch.float64, device=XY.device)
+    res = (hb_result * P)()
+    _check(L.hb_triage_features(ctx.handle, P, _dev(XY), na, ma, XY.shape[1], _dtype_code(XY), C.byref(opts),
+                                _dev(feat), _dev(tobs), res, _stream(stream)))
+    return feat, tobs, [r.as_dict() for r in res]
+
+
+def null_quantiles(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, stream=None):
+    """(quantiles of |T_b| x100 [P][9] float32, results) from the full test."""
+    L = lib()
+    vp = C.c_void_p
+    L.hb_null_quantiles.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_int64, C.c_int32, C.POINTER(hb_opts), vp,
+                                    C.POINTER(hb_result), vp]
+    L.hb_null_quantiles.restype = C.c_int
+    P, na, ma = _batched_args(XY, n, m)
+    q = torch.empty((P, TRIAGE_NQ), dtype=torch.float32, device=XY.device)
+    res = (hb_result * P)()
+    _check(L.hb_null_quantiles(ctx.handle, P, _dev(XY), na, ma, XY.shape[1], _dtype_code(XY), C.byref(opts),
+                               _dev(q), res, _stream(stream)))
+    return q, [r.as_dict() for r in res]
+
+
+def mlp_param_count() -> int:
+    L = lib()
+    L.hb_mlp_param_count.argtypes = []
+    L.hb_mlp_param_count.restype = C.c_int64
+    return int(L.hb_mlp_param_count())
+
+
+class MLP:
+    """Device buffers of the triage network (the library's kernels do all math)."""
+
+    def __init__(self, params: torch.Tensor):
+        n = mlp_param_count()
+        assert params.numel() == n and params.dtype == torch.float32 and params.is_cuda
+        dev = params.device
+        self.params = params.contiguous()
+        self.params_bf16 = torch.empty(n, dtype=torch.int16, device=dev)
+        self.grad = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.adam_m = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.adam_v = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.step = 0
+        self._net = hb_mlp(self.params.data_ptr(), self.params_bf16.data_ptr(), self.grad.data_ptr(),
+                           self.adam_m.data_ptr(), self.adam_v.data_ptr())
+        L = lib()
+        L.hb_mlp_sync.argtypes = [C.POINTER(hb_mlp), C.c_void_p]
+        L.hb_mlp_sync.restype = C.c_int
+        _check(L.hb_mlp_sync(C.byref(self._net), _stream()))
+
+    def forward(self, ctx: Context, feat: torch.Tensor, stream=None) -> torch.Tensor:
+        L = lib()
+        L.hb_mlp_forward.argtypes = [C.c_void_p, C.POINTER(hb_mlp), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.hb_mlp_forward.restype = C.c_int
+        out = torch.empty((feat.shape[0], TRIAGE_NQ), dtype=torch.float32, device=feat.device)
+        _check(L.hb_mlp_forward(ctx.handle, C.byref(self._net), feat.shape[0], _dev(feat), _dev(out), _stream(stream)))
+        return out
+
+    def grad_step(self, ctx: Context, feat: torch.Tensor, target: torch.Tensor, stream=None) -> torch.Tensor:
+        """Fills self.grad with the gradient of the mean pinball loss; returns the loss (device)."""
+        L = lib()
+        L.hb_mlp_grad.argtypes = [C.c_void_p, C.POINTER(hb_mlp), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]
+        L.hb_mlp_grad.restype = C.c_int
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        _check(L.hb_mlp_grad(ctx.handle, C.byref(self._net), feat.shape[0], _dev(feat), _dev(target), _dev(loss),
+                             _stream(stream)))
+        return loss
+
+    def adam(self, lr: float, stream=None):
+        L = lib()
+        L.hb_mlp_adam.argtypes = [C.POINTER(hb_mlp), C.c_float, C.c_int64, C.c_void_p]
+        L.hb_mlp_adam.restype = C.c_int
+        self.step += 1
+        _check(L.hb_mlp_adam(C.byref(self._net), lr, self.step, _stream(stream)))
+
+
+def triage_predict_p(quant: torch.Tensor, tobs: torch.Tensor, stream=None) -> torch.Tensor:
+    L = lib()
+    L.hb_triage_predict_p.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.hb_triage_predict_p.restype = C.c_int
+    p = torch.empty(quant.shape[0], dtype=torch.float32, device=quant.device)
+    _check(L.hb_triage_predict_p(quant.shape[0], _dev(quant), _dev(tobs), _dev(p), _stream(stream)))
+    return p

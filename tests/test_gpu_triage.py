@@ -1,0 +1,130 @@
+"""GPU tests of the learned triage: features, null-quantile targets, the
+network's forward and backward passes and Adam against the FP64 numpy oracle
+on the same seeded inputs, then an end-to-end run that trains the network on
+the library's own permutation runs and measures what it gains."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from oracle import triage_oracle as TO  # noqa: E402
+from paper_2605_08048_gb300 import hbperm as H  # noqa: E402
+from paper_2605_08048_gb300 import synth  # noqa: E402
+from paper_2605_08048_gb300 import triage as TR  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    if a.dtype == np.uint16:
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("d,dtype", [(768, "bf16"), (100, "bf16"), (1000, "f32"), (250, "f32"), (1024, "bf16")],
+                         ids=["768-bf16", "100-bf16-unaligned-rows", "1000-f32", "250-f32-unaligned-rows",
+                              "1024-bf16"])
+def test_features_match_oracle(ctx, d, dtype):
+    b = synth.batch(61, 4, d=d, dtype=dtype, sizes=([120, 300, 45, 800], [200, 90, 60, 700]))
+    f, tobs, res = H.triage_features(ctx, _dev(b.XY), b.n, b.m, H.make_opts())
+    f = f.cpu().numpy().astype(np.float64)
+    for p in range(4):
+        X, Y = b.pair(p)
+        r, _, _ = O.perm_test(X, Y, O.opts(B=1))
+        assert res[p]["status"] == 0 and res[p]["T_obs"] == pytest.approx(r["T_obs"], rel=1e-12, abs=1e-15)
+        want = TO.features(X, Y, r["T_obs"])
+        assert np.abs(f[p, :2] - want[:2]).max() < 1e-6
+        assert np.abs(f[p, 2:18] - want[2:18]).max() < 2e-3  # log Ritz values, FP32 iterations vs FP64
+        assert abs(f[p, 18] - want[18]) < 1e-5
+
+
+def test_null_quantiles_match_oracle(ctx):
+    b = synth.batch(62, 3, d=128, dtype="bf16", sizes=([40, 150, 77], [60, 90, 33]))
+    q, res = H.null_quantiles(ctx, _dev(b.XY), b.n, b.m, H.make_opts(B=2000, seed=4))
+    q = q.cpu().numpy().astype(np.float64)
+    for p in range(3):
+        X, Y = b.pair(p)
+        r, T, _ = O.perm_test(X, Y, O.opts(B=2000, seed=4), want_T=True)
+        assert res[p]["count"] == r["count"]
+        want = 100.0 * TO.null_quantiles(T)
+        assert np.abs(q[p] - want).max() <= 1e-3 * (1 + np.abs(want).max())
+
+
+def _net_and_data(seed=7, P=300):
+    rng = np.random.default_rng(seed)
+    params = TR.init_params(seed).cpu().numpy().astype(np.float64)
+    F = rng.standard_normal((P, TO.N_FEAT)).astype(np.float32)
+    T = np.abs(rng.standard_normal((P, TO.N_OUT))).astype(np.float32) * 5
+    return params, F, T
+
+
+def test_mlp_forward_matches_oracle(ctx):
+    params, F, _ = _net_and_data()
+    net = H.MLP(torch.from_numpy(params.astype(np.float32)).cuda())
+    y = net.forward(ctx, _dev(F)).cpu().numpy().astype(np.float64)
+    want, _ = TO.mlp_forward(params, F.astype(np.float64))
+    assert np.abs(y - want).max() <= 1e-4 * (1 + np.abs(want).max())
+
+
+def test_mlp_gradient_matches_oracle(ctx):
+    params, F, T = _net_and_data(P=1500)
+    net = H.MLP(torch.from_numpy(params.astype(np.float32)).cuda())
+    loss = net.grad_step(ctx, _dev(F), _dev(T))
+    g = net.grad.cpu().numpy().astype(np.float64)
+    y, cache = TO.mlp_forward(params, F.astype(np.float64))
+    lref, dy = TO.pinball(y, T.astype(np.float64))
+    gref = TO.mlp_backward(params, cache, dy)
+    assert abs(float(loss) - lref) <= 1e-5 * (1 + abs(lref))
+    for a, b in zip(TO.unpack(g), TO.unpack(gref)):
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-7
+
+
+def test_adam_step_matches_oracle(ctx):
+    params, F, T = _net_and_data(P=256)
+    net = H.MLP(torch.from_numpy(params.astype(np.float32)).cuda())
+    net.grad_step(ctx, _dev(F), _dev(T))
+    g = net.grad.cpu().numpy().astype(np.float64)
+    net.adam(1e-3)
+    got = net.params.cpu().numpy().astype(np.float64)
+    want, _, _ = TO.adam(params.astype(np.float32).astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1,
+                         lr=1e-3)
+    assert np.abs(got - want).max() <= 1e-6
+
+
+def test_predict_p_matches_oracle(ctx):
+    rng = np.random.default_rng(9)
+    q = np.sort(np.abs(rng.standard_normal((50, 9))) * 3, axis=1).astype(np.float32)
+    q[::7] = q[::7, ::-1]  # some non-monotone rows
+    tobs = (rng.standard_normal(50) * 0.05).astype(np.float64)
+    p = H.triage_predict_p(_dev(q), _dev(tobs)).cpu().numpy()
+    for i in range(50):
+        want = TO.predict_p(q[i].astype(np.float64) / 100.0, abs(tobs[i]))
+        assert abs(p[i] - want) <= 1e-6
+
+
+def test_triage_gains_over_testing_every_pair(ctx):
+    """Train on the library's own runs of 8192 pairs, triage 2048 held-out
+    pairs at alpha = 0.05 with the [0.005, 0.2] band and a 2 % audit."""
+    opts = H.make_opts(B=9999, seed=1)
+    train_b = [synth.workload_batched(seed=500 + k, P=1024) for k in range(8)]
+    feat, target = TR.training_set(ctx, train_b, opts)
+    net, hist = TR.train(ctx, feat, target, epochs=80, batch=1024, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    held_out = synth.workload_batched(seed=900, P=2048)
+    TR.triage(ctx, net, held_out, opts, evaluate_all=False)  # warm-up: workspace sizing
+    rep = TR.triage(ctx, net, held_out, opts)
+    print(f"\ntriage: loss {hist[0]:.4f} -> {hist[-1]:.4f}; {rep.skipped}/{rep.pairs} pairs skip the full test, "
+          f"audit error {rep.audit_decision_error:.3f} ({rep.audited} audited), error on skipped pairs "
+          f"{rep.decision_error_skipped:.4f}; features {rep.seconds_features:.3f} s + subset test "
+          f"{rep.seconds_full_subset:.3f} s vs all pairs {rep.seconds_full_all:.3f} s")
+    assert rep.skipped >= 0.4 * rep.pairs
+    assert rep.decision_error_skipped <= 0.05
+    assert rep.seconds_features + rep.seconds_full_subset < rep.seconds_full_all
