@@ -67,14 +67,18 @@ struct hb_ctx {
     cudaEvent_t tev[7] = {};
     float last_ms[6] = {};
     int last_launches = 0;
-    // side stream for the label draws, which depend on no data and overlap
-    // the alignment stages (fork/join with events on the caller's stream)
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // Streams of a call: the caller's stream forks into `main` (highest
+    // priority) and joins back at the end; the label draws, which depend on no
+    // data, run on `side` (lowest priority) and fill the SMs the alignment
+    // kernels leave free instead of holding them back.
+    cudaStream_t main = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, enter = nullptr, leave = nullptr;
     // relabelling statistics of hb_null_quantiles
     void *tbuf = nullptr;
     size_t tbuf_cap = 0;
 };
+
+extern "C" void hb_ctx_destroy(hb_ctx *c);
 
 static void mark(hb_ctx *c, int k, cudaStream_t s)
 {
@@ -91,12 +95,17 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
     hb_ctx *c = new hb_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess ||
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
-        return fail(HB_ERR_CUDA, "cudaEventCreate failed");
+        cudaEventCreateWithFlags(&c->enter, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->leave, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->main, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess) {
+        hb_ctx_destroy(c);
+        return fail(HB_ERR_CUDA, "stream or event creation failed");
     }
     *out = c;
     g_err.clear();
@@ -113,12 +122,13 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
     }
     for (int k = 0; k < 7; ++k)
         if (c->tev[k]) cudaEventDestroy(c->tev[k]);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        cudaStreamDestroy(c->side);
-    }
-    if (c->fork) cudaEventDestroy(c->fork);
-    if (c->join) cudaEventDestroy(c->join);
+    for (cudaStream_t q : {c->main, c->side})
+        if (q) {
+            cudaStreamSynchronize(q);
+            cudaStreamDestroy(q);
+        }
+    for (cudaEvent_t e : {c->fork, c->join, c->enter, c->leave})
+        if (e) cudaEventDestroy(e);
     if (c->tbuf) cudaFree(c->tbuf);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFreeHost(c->stage);
@@ -383,9 +393,9 @@ struct TriageOut {
     float *quant = nullptr;  // null-quantile mode: [P][9] quantiles of |T_b| (x100), T_out required
 };
 
-static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
-                     bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
-                     cudaStream_t s, std::vector<PairOut> &out, const TriageOut *tri = nullptr)
+static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
+                        bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
+                        cudaStream_t s, std::vector<PairOut> &out, const TriageOut *tri)
 {
     const bool features = tri && tri->feat;
     set_attrs(c);
@@ -410,9 +420,9 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         carve(cv, b, pl, align_only, Z_out == nullptr, xy_bytes, cap, rgrid);
         void *Z = Z_out ? Z_out : b.Z;
 
-        // input staging (host memory) and pair pointers
+        // pair pointers into the device copy of host input (copied below, after
+        // the label draws are forked: they need only the metadata)
         if (xy_host) {
-            CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
             for (int p = 0; p < P; ++p) {
                 pl.meta[p].X = (const char *)b.xy + (size_t)xy_row_off[p] * d * esz;
                 pl.meta[p].Y = (const char *)pl.meta[p].X + (size_t)pl.meta[p].n * d * esz;
@@ -442,6 +452,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
             launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, c->side);
             CK(cudaEventRecord(c->join, c->side));
         }
+        if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
         if (!align_only) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
         if (!align_only) CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
         if (mixed && o.d_pad != d)
@@ -558,6 +569,22 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
         return HB_OK;
     }
     return fail(HB_ERR_CUDA, "recheck list kept overflowing");
+}
+
+// One call: fork the caller's stream into the context's main stream, run,
+// join back (also on failure), so that work the caller queues afterwards sees
+// every output.
+static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
+                     bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
+                     cudaStream_t user, std::vector<PairOut> &out, const TriageOut *tri = nullptr)
+{
+    CK(cudaEventRecord(c->enter, user));
+    CK(cudaStreamWaitEvent(c->main, c->enter, 0));
+    const hb_status hs = run_on(c, pl, xy_host, xy_bytes, xy_row_off, align_only, Z_out, u_out, skipped_out, T_out,
+                                c->main, out, tri);
+    CK(cudaEventRecord(c->leave, c->main));
+    CK(cudaStreamWaitEvent(user, c->leave, 0));
+    return hs;
 }
 
 static void fill_result(const PairOut &r, hb_result *o)

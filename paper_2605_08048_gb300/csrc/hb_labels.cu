@@ -81,7 +81,7 @@ __global__ void k_labels_pipeline(const PairMeta *__restrict__ meta, const PairS
         for (int w = 0; w < pm.W; ++w) col[(int64_t)w * pm.B_pad] = 0u;
         return;
     }
-    for (int w = 0; w < pm.W; ++w) col[(int64_t)w * pm.B_pad] = 0u;
+    // the walk emits every word 0..W-1 exactly once
     walk_labels(seed, stream, pm.n, pm.N, (uint64_t)b, [&](int w, uint32_t v) { col[(int64_t)w * pm.B_pad] = v; });
 }
 

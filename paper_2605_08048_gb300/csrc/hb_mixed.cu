@@ -37,6 +37,7 @@ namespace hb {
 constexpr int MX_M = 128;            // relabellings per tile (TMEM lanes)
 constexpr int MX_K = 64;             // tokens per stage (one 128-byte swizzle atom of BF16)
 constexpr int MX_NS = 4;             // pipeline stages
+constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
 constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB
 constexpr int MX_STAGE_BYTES = 48 * 1024;         // A + up to 256 B-rows x 128 B
 constexpr int MX_THREADS = 320;
@@ -403,10 +404,15 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                 lo = w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
                 hi = w0 + 1 < pm.W ? __ldg(lab + (int64_t)(w0 + 1) * pm.B_pad) : 0u;
             };
-            // loads run two stages ahead of the expansion, across column tiles
-            uint32_t lo_cur, hi_cur, lo_nxt, hi_nxt;
-            words(0, lo_cur, hi_cur);
-            words(KC > 1 ? 1 : 0, lo_nxt, hi_nxt);
+            // loads run MX_PF stages ahead of the expansion (a register ring,
+            // wrapping across column tiles), which covers the DRAM latency
+            uint32_t rlo[MX_PF], rhi[MX_PF];
+            int knext = 0;  // K-chunk of the next load
+#pragma unroll
+            for (int i = 0; i < MX_PF; ++i) {
+                words(knext, rlo[i], rhi[i]);
+                if (++knext == KC) knext = 0;
+            }
             for (int c = 0; c < C && ok; ++c) {
                 for (int kc = 0; kc < KC; ++kc) {
                     // warp-uniform outcome, so the __syncwarp below is always complete
@@ -414,10 +420,14 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                         ok = false;
                         break;
                     }
-                    const uint32_t lo = lo_cur, hi = hi_cur;
-                    lo_cur = lo_nxt;
-                    hi_cur = hi_nxt;
-                    words((kc + 2) % KC, lo_nxt, hi_nxt);
+                    const uint32_t lo = rlo[0], hi = rhi[0];
+#pragma unroll
+                    for (int i = 0; i + 1 < MX_PF; ++i) {
+                        rlo[i] = rlo[i + 1];
+                        rhi[i] = rhi[i + 1];
+                    }
+                    words(knext, rlo[MX_PF - 1], rhi[MX_PF - 1]);
+                    if (++knext == KC) knext = 0;
                     uint8_t *row = smem + stage * MX_STAGE_BYTES + r * 128;
 #pragma unroll
                     for (int ch = 0; ch < 8; ++ch) {
