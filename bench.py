@@ -262,6 +262,26 @@ def main():
     e2e = {"value": world * P * e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(XYh.numel() * 2),
            "d2h_bytes_per_step": int(P * 80 + 16)}
 
+    # the same batch through a plan: one CUDA graph replay per step, identical counts
+    plan = H.Plan(ctx, n, m, a.d, torch.bfloat16, opts)
+    plan.execute(XY)
+    barrier()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(a.steps):
+        rg = plan.execute(XY)
+    h1.record(stream)
+    barrier()
+    tg = h0.elapsed_time(h1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([tg], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tg = float(tt.item())
+    assert [r["count"] for r in rg] == counts
+    graph = {"value": world * P * a.steps / tg, "unit": UNIT, "ms_per_step": 1000.0 * tg / a.steps,
+             "api": "hb_plan_execute (CUDA graph of the whole test)"}
+    plan.close()
+
     # the plain FP32 GPU path on the same workload: throughput and identical counts
     plain = None
     if not a.no_plain and path == H.HB_PATH_MIXED:
@@ -298,6 +318,7 @@ def main():
         "stage_ms": stage_ms,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "graph": graph,
         "plain_fp32": plain,
         "rechecked_per_step": int(sum(r["n_rechecked"] for r in res)),
         "gpu_launches": launches,

@@ -106,6 +106,7 @@ typedef struct {
 } hb_result;
 
 typedef struct hb_ctx hb_ctx;
+typedef struct hb_plan hb_plan;
 
 /* Create a context bound to CUDA device `device`.  It owns the device
  * workspace (grown on demand), pinned staging buffers and captured graphs.
@@ -138,6 +139,32 @@ hb_status hb_perm_test(hb_ctx *ctx, const void *X, int64_t n, const void *Y, int
  * pairs are independent, so one pair's failure leaves the others valid. */
 hb_status hb_perm_test_batched(hb_ctx *ctx, int64_t P, const void *XY, const int64_t *n, const int64_t *m,
                                int64_t d, int32_t dtype, const hb_opts *opts, hb_result *out, void *stream);
+
+/* A batch shape planned once and replayed as one CUDA graph.  The label
+ * draws, the work list and every launch of a test depend only on the group
+ * sizes and opts, never on the data (Sec. 3.2, "Reusability"), so
+ * hb_plan_create builds the work list for sizes n, m (host, P entries) and
+ * opts, allocates the plan's own device workspace and pinned host staging,
+ * and captures every device stage of the call -- label draws, alignment,
+ * statistics, the group-sum GEMM with its fused decision, the exact recheck,
+ * finalize and the copy of the results -- in one CUDA graph.  The plan keeps
+ * ctx (which must outlive it) and no caller memory.  HB_ERR_OOM when the
+ * workspace cannot be allocated; other errors as hb_perm_test_batched. */
+hb_status hb_plan_create(hb_ctx *ctx, int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
+                         const hb_opts *opts, hb_plan **plan);
+
+/* Runs the planned test on XY (device or host, packed as for
+ * hb_perm_test_batched with the plan's sizes; for host XY the bytes are
+ * copied into a plan-owned device buffer first) with one graph launch on
+ * `stream`.  The pair pointers are re-uploaded only when XY differs from the
+ * previous call's.  out (host, P entries): results identical to
+ * hb_perm_test_batched's.  Synchronises `stream`; calls on one plan must not
+ * overlap.  If the exact-recheck list outgrows the capacity planned for it,
+ * the call reruns through hb_perm_test_batched (same results, no graph). */
+hb_status hb_plan_execute(hb_plan *plan, const void *XY, hb_result *out, void *stream);
+
+/* Frees the plan's graph, streams, workspace and staging (NULL is a no-op). */
+void hb_plan_destroy(hb_plan *plan);
 
 /* HB-LABEL-v1 label rows for relabellings b0 .. b0+count-1 of a pool of N
  * with group-1 size n (Sec. 3.2: the sign matrix S with exactly n entries

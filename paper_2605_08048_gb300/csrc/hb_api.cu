@@ -393,11 +393,132 @@ struct TriageOut {
     float *quant = nullptr;  // null-quantile mode: [P][9] quantiles of |T_b| (x100), T_out required
 };
 
+// Handles a call's device stages are enqueued with.
+struct Exec {
+    cudaStream_t s, side;    // main stream; the label draws run on `side`
+    cudaEvent_t fork, join;  // side-stream fork/join
+    cudaEvent_t *tev;        // 7 stage events, or nullptr
+    int sms;
+    bool capture = false;    // enqueued under stream capture (events become graph nodes)
+};
+
+static void xmark(const Exec &ex, int k)
+{
+    if (ex.tev) cudaEventRecordWithFlags(ex.tev[k], ex.s, ex.capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// Every device stage of a permutation test after the metadata upload: label
+// draws (side stream), steps 1-5 of the path, finalize and the copy of the
+// counters (host_out + 0) and per-pair results (host_out + 64) to pinned host
+// memory.  Nothing here synchronises the host, so a stream capture of this
+// function is a CUDA graph of the whole call.
+static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, void *Z, const void *xy_host,
+                              size_t xy_bytes, float *T_out, const TriageOut *tri, unsigned int cap, int rgrid,
+                              void *host_out)
+{
+    const bool features = tri && tri->feat;
+    const cudaStream_t s = ex.s;
+    const int P = pl.P;
+    const RunOpts &o = pl.o;
+    const int d = o.d;
+    const bool mixed = o.path == HB_PATH_MIXED;
+    if (!features) {
+        // labels on the side stream from here on, concurrently with steps 1-4
+        CK(cudaEventRecord(ex.fork, s));
+        CK(cudaStreamWaitEvent(ex.side, ex.fork, 0));
+        launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, ex.side);
+        CK(cudaEventRecord(ex.join, ex.side));
+    }
+    if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
+    CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
+    if (mixed && o.d_pad != d)
+        CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
+
+    const unsigned int nch = (unsigned int)pl.chunks.size();
+    // steps 1-3 (column maxima feed the slice scales and the exact-sum windows)
+    xmark(ex, 0);
+    launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
+    launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
+    launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, b.colmax, s);
+    CK(cudaGetLastError());
+
+    // step 4: Z statistics, fixed-point slices, T_obs
+    const int64_t zq_ld = pl.total_rows_pad;
+    xmark(ex, 1);
+    launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o, b.cc,
+                  s);
+    launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
+    CK(cudaGetLastError());
+
+    if (features) {
+        xmark(ex, 2);
+        xmark(ex, 3);
+        launch_features(b.meta, P, o, b.st, Z, b.lam, tri->feat, tri->tobs, s);
+        xmark(ex, 4);
+    } else {
+        // step 5: labels, group sums + statistic + band, exact recheck
+        xmark(ex, 2);
+        CK(cudaStreamWaitEvent(s, ex.join, 0));  // the "labels" stage is the part not hidden
+        xmark(ex, 3);
+        CK(cudaGetLastError());
+        if (mixed) {
+            MixedArgs ma{};
+            ma.meta = b.meta;
+            ma.P = P;
+            ma.o = o;
+            ma.st = b.st;
+            ma.cc = b.cc;
+            ma.bits = b.bits;
+            ma.zq = b.zq;
+            ma.zq_ld = zq_ld;
+            ma.zq_rows = (int64_t)o.slices * o.d_pad;
+            ma.list = b.list;
+            ma.n_items = b.counters;
+            ma.cap = cap;
+            ma.overflow = b.counters + 1;
+            ma.timeout = b.counters + 2;
+            ma.T_out = T_out;
+            ma.items = b.items;
+            ma.n_work = (int)pl.items.size();
+            ma.sms = ex.sms;
+            std::string err;
+            const cudaError_t e = launch_mixed(ma, s, err);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
+                            "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
+            }
+        } else {
+            launch_plain(b.meta, P, pl.max_Bpad, o, b.st, Z, b.cc, b.bits, b.list, b.counters, cap, b.counters + 1,
+                         T_out, s);
+        }
+        CK(cudaGetLastError());
+        xmark(ex, 4);
+        launch_recheck(cap, (unsigned int)rgrid, pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.colmax, b.bits, b.list,
+                       b.counters, b.scratch, T_out, s);
+    }
+    xmark(ex, 5);
+    launch_finalize(b.meta, P, o, b.st, b.out, s);
+    if (tri && tri->quant) {
+        int64_t maxB = 1;
+        for (int p = 0; p < P; ++p) maxB = std::max<int64_t>(maxB, pl.meta[p].B);
+        launch_null_quantiles(b.meta, P, (int)maxB, T_out, b.st, 100.0f, tri->quant, s);
+    }
+    CK(cudaGetLastError());
+
+    // one copy back: results and the counters
+    char *h = (char *)host_out;
+    CK(cudaMemcpyAsync(h, b.counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + 64, b.out, sizeof(PairOut) * P, cudaMemcpyDeviceToHost, s));
+    xmark(ex, 6);
+    return HB_OK;
+}
+
 static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, const int64_t *xy_row_off,
                         bool align_only, void *Z_out, double *u_out, int32_t *skipped_out, float *T_out,
                         cudaStream_t s, std::vector<PairOut> &out, const TriageOut *tri)
 {
-    const bool features = tri && tri->feat;
     set_attrs(c);
     const int P = pl.P;
     const RunOpts o = pl.o;
@@ -431,7 +552,7 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         // metadata upload through pinned staging
         const size_t mbytes = sizeof(PairMeta) * P, cbytes = sizeof(RowChunk) * pl.chunks.size(),
                      bbytes = sizeof(int) * P, ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0;
-        hs = ensure_stage(c, mbytes + cbytes + bbytes + ibytes + 64);
+        hs = ensure_stage(c, std::max(mbytes + cbytes + bbytes + ibytes, sizeof(PairOut) * P) + 64);
         if (hs != HB_OK) return hs;
         char *hs_ = (char *)c->stage;
         memcpy(hs_, pl.meta.data(), mbytes);
@@ -445,29 +566,14 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             CK(cudaMemcpyAsync(b.items, hs_ + mbytes + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, s));
         }
         CK(cudaEventRecord(c->stage_done, s));
-        if (!align_only && !features) {
-            // labels on the side stream from here on, concurrently with steps 1-4
-            CK(cudaEventRecord(c->fork, s));
-            CK(cudaStreamWaitEvent(c->side, c->fork, 0));
-            launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, c->side);
-            CK(cudaEventRecord(c->join, c->side));
-        }
-        if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
-        if (!align_only) CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
-        if (!align_only) CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
-        if (mixed && o.d_pad != d)
-            CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
-
-        const unsigned int nch = (unsigned int)pl.chunks.size();
-        // steps 1-3
-        mark(c, 0, s);
-        launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
-        launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
-        unsigned int *colmax = align_only ? nullptr : b.colmax;  // column maxima: slice scales and exact-sum windows
-        launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, colmax, s);
-        CK(cudaGetLastError());
-
         if (align_only) {
+            if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
+            const unsigned int nch = (unsigned int)pl.chunks.size();
+            mark(c, 0, s);
+            launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
+            launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
+            launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, nullptr, s);
+            CK(cudaGetLastError());
             if (u_out) CK(cudaMemcpyAsync(u_out, b.u, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
             if (skipped_out) {
                 PairState hst;
@@ -479,78 +585,11 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             }
             return HB_OK;
         }
-
-        // step 4: Z statistics, fixed-point slices, T_obs
-        const int64_t zq_ld = pl.total_rows_pad;
-        mark(c, 1, s);
-        launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o,
-                      b.cc, s);
-        launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
-        CK(cudaGetLastError());
-
-        if (features) {
-            mark(c, 2, s);
-            mark(c, 3, s);
-            launch_features(b.meta, P, o, b.st, Z, b.lam, tri->feat, tri->tobs, s);
-            mark(c, 4, s);
-        } else {
-        // step 5: labels, group sums + statistic + band, exact recheck
-        mark(c, 2, s);
-        CK(cudaStreamWaitEvent(s, c->join, 0));  // the "labels" stage is the part not hidden
-        mark(c, 3, s);
-        CK(cudaGetLastError());
-        if (mixed) {
-            MixedArgs ma{};
-            ma.meta = b.meta;
-            ma.P = P;
-            ma.o = o;
-            ma.st = b.st;
-            ma.cc = b.cc;
-            ma.bits = b.bits;
-            ma.zq = b.zq;
-            ma.zq_ld = zq_ld;
-            ma.zq_rows = (int64_t)o.slices * o.d_pad;
-            ma.list = b.list;
-            ma.n_items = b.counters;
-            ma.cap = cap;
-            ma.overflow = b.counters + 1;
-            ma.timeout = b.counters + 2;
-            ma.T_out = T_out;
-            ma.items = b.items;
-            ma.n_work = (int)pl.items.size();
-            ma.sms = c->sms;
-            std::string err;
-            const cudaError_t e = launch_mixed(ma, s, err);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
-                            "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
-            }
-        } else {
-            launch_plain(b.meta, P, pl.max_Bpad, o, b.st, Z, b.cc, b.bits, b.list, b.counters, cap, b.counters + 1,
-                         T_out, s);
-        }
-        CK(cudaGetLastError());
-        mark(c, 4, s);
-        launch_recheck(cap, (unsigned int)rgrid, pl.max_W, b.meta, o, b.st, Z, b.t_ex, b.colmax, b.bits, b.list,
-                       b.counters, b.scratch, T_out, s);
-        }
-        mark(c, 5, s);
-        launch_finalize(b.meta, P, o, b.st, b.out, s);
-        if (tri && tri->quant) {
-            int64_t maxB = 1;
-            for (int p = 0; p < P; ++p) maxB = std::max<int64_t>(maxB, pl.meta[p].B);
-            launch_null_quantiles(b.meta, P, (int)maxB, T_out, b.st, 100.0f, tri->quant, s);
-        }
-        CK(cudaGetLastError());
-
-        // one copy back: results and the counters
-        hs = ensure_stage(c, sizeof(PairOut) * P + 64);
+        // results come back through the same pinned staging (after the metadata copies)
+        const Exec ex{s, c->side, c->fork, c->join, c->timing ? c->tev : nullptr, c->sms};
+        hs = enqueue_test(ex, pl, b, Z, xy_host, xy_bytes, T_out, tri, cap, rgrid, c->stage);
         if (hs != HB_OK) return hs;
         char *h = (char *)c->stage;
-        CK(cudaMemcpyAsync(h, b.counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 64, b.out, sizeof(PairOut) * P, cudaMemcpyDeviceToHost, s));
-        mark(c, 6, s);
         CK(cudaStreamSynchronize(s));
         const unsigned int *cnt = (const unsigned int *)h;
         if (cnt[2]) return fail(HB_ERR_TIMEOUT, "a bounded device wait expired in the mixed path");
@@ -705,6 +744,212 @@ extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, 
         fill_result(out[p], &res[p]);
         if (out[p].status != HB_OK && first == HB_OK) first = (hb_status)out[p].status;
     }
+    if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
+    g_err.clear();
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planned batches: the device stages of one batch shape as a CUDA graph
+// ---------------------------------------------------------------------------
+struct hb_plan {
+    hb_ctx *c = nullptr;
+    Plan pl;
+    hb_opts opts{};
+    std::vector<int64_t> n, m, off;
+    int64_t d = 0;
+    int32_t dtype = 0;
+    size_t esz = 2, xy_bytes = 0, res_bytes = 0, mbytes = 0;
+    unsigned int cap = 0;
+    int rgrid = 1;
+    Bufs b{};
+    void *ws = nullptr;
+    void *xy_dev = nullptr;       // device copy of host input
+    char *host = nullptr;         // pinned: [counters + results][pair metadata]
+    const void *bound = nullptr;  // input the uploaded pair pointers refer to
+    cudaStream_t cs = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t tev[7] = {};
+    bool timed = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+extern "C" void hb_plan_destroy(hb_plan *q)
+{
+    if (!q) return;
+    if (q->c) cudaSetDevice(q->c->device);
+    for (cudaStream_t st : {q->cs, q->side})
+        if (st) cudaStreamSynchronize(st);
+    if (q->exec) cudaGraphExecDestroy(q->exec);
+    if (q->graph) cudaGraphDestroy(q->graph);
+    for (cudaStream_t st : {q->cs, q->side})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {q->fork, q->join})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : q->tev)
+        if (e) cudaEventDestroy(e);
+    if (q->ws) cudaFree(q->ws);
+    if (q->xy_dev) cudaFree(q->xy_dev);
+    if (q->host) cudaFreeHost(q->host);
+    delete q;
+}
+
+static hb_status plan_build(hb_plan *q, int64_t P)
+{
+    hb_ctx *c = q->c;
+    Plan &pl = q->pl;
+    hb_status hs = make_plan(pl, P, q->n.data(), q->m.data(), q->d, q->dtype, q->opts, false, false);
+    if (hs != HB_OK) return hs;
+    const bool mixed = pl.o.path == HB_PATH_MIXED;
+    q->esz = q->dtype == HB_F32 ? 4 : 2;
+    q->off.assign(P + 1, 0);
+    for (int64_t p = 0; p < P; ++p) q->off[p + 1] = q->off[p] + q->n[p] + q->m[p];
+    q->xy_bytes = (size_t)q->off[P] * q->d * q->esz;
+    q->cap = (unsigned int)std::min<int64_t>((int64_t)1 << 30, (mixed ? pl.total_B / 256 : pl.total_B / 16) + 4096);
+    q->rgrid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(q->cap, (int64_t)(256u << 20) / (int64_t)(2 * sizeof(double) * pl.o.d)));
+
+    // own workspace and pinned staging
+    Carve probe(nullptr);
+    const size_t need = carve(probe, q->b, pl, false, true, 0, q->cap, q->rgrid);
+    if (cudaMalloc(&q->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        q->ws = nullptr;
+        return fail(HB_ERR_OOM, "plan workspace of %zu bytes", need);
+    }
+    Carve cv(q->ws);
+    carve(cv, q->b, pl, false, true, 0, q->cap, q->rgrid);
+    q->mbytes = sizeof(PairMeta) * P;
+    const size_t cbytes = sizeof(RowChunk) * pl.chunks.size(), bbytes = sizeof(int) * P,
+                 ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0;
+    q->res_bytes = (64 + sizeof(PairOut) * P + 255) & ~(size_t)255;
+    const size_t host_bytes = q->res_bytes + std::max(q->mbytes, cbytes + bbytes + ibytes) + 64;
+    if (cudaMallocHost((void **)&q->host, host_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        q->host = nullptr;
+        return fail(HB_ERR_OOM, "plan staging of %zu bytes", host_bytes);
+    }
+
+    int prio_least = 0, prio_greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    CK(cudaStreamCreateWithPriority(&q->cs, cudaStreamNonBlocking, prio_greatest));
+    CK(cudaStreamCreateWithPriority(&q->side, cudaStreamNonBlocking, prio_least));
+    CK(cudaEventCreateWithFlags(&q->fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&q->join, cudaEventDisableTiming));
+    q->timed = c->timing;
+    if (q->timed)
+        for (cudaEvent_t &e : q->tev) CK(cudaEventCreate(&e));
+
+    // the metadata that does not depend on the input address, once
+    char *h = q->host + q->res_bytes;
+    memcpy(h, pl.chunks.data(), cbytes);
+    memcpy(h + cbytes, pl.init_bad.data(), bbytes);
+    if (ibytes) memcpy(h + cbytes + bbytes, pl.items.data(), ibytes);
+    CK(cudaMemcpyAsync(q->b.chunks, h, cbytes, cudaMemcpyHostToDevice, q->cs));
+    CK(cudaMemcpyAsync(q->b.bad, h + cbytes, bbytes, cudaMemcpyHostToDevice, q->cs));
+    if (ibytes) CK(cudaMemcpyAsync(q->b.items, h + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, q->cs));
+    CK(cudaStreamSynchronize(q->cs));
+
+    // capture every device stage of the call
+    CK(cudaStreamBeginCapture(q->cs, cudaStreamCaptureModeRelaxed));
+    Exec ex{q->cs, q->side, q->fork, q->join, q->timed ? q->tev : nullptr, c->sms};
+    ex.capture = true;
+    hs = enqueue_test(ex, pl, q->b, q->b.Z, nullptr, 0, nullptr, nullptr, q->cap, q->rgrid, q->host);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(q->cs, &g);
+    if (hs != HB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return hs;
+    }
+    if (ce != cudaSuccess || !g) return fail(HB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    q->graph = g;
+    CK(cudaGraphInstantiateWithFlags(&q->exec, g, cudaGraphInstantiateFlagUseNodePriority));
+    const int pchunks = (int)((P + 65534) / 65535);
+    q->launches = 8 + pchunks + (mixed ? 1 : pchunks) + 2 * (int)((q->cap + q->rgrid - 1) / q->rgrid);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_plan_create(hb_ctx *c, int64_t P, const int64_t *n, const int64_t *m, int64_t d,
+                                    int32_t dtype, const hb_opts *opts, hb_plan **out)
+{
+    if (!c || !out) return fail(HB_ERR_INVALID_ARG, "ctx and plan must be non-NULL");
+    *out = nullptr;
+    if (P < 1 || P > (1 << 24)) return fail(HB_ERR_INVALID_ARG, "P = %lld", (long long)P);
+    if (!n || !m || !opts) return fail(HB_ERR_INVALID_ARG, "n, m and opts must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    CK(cudaSetDevice(c->device));
+    set_attrs(c);
+    hb_plan *q = new hb_plan();
+    q->c = c;
+    q->opts = *opts;
+    q->d = d;
+    q->dtype = dtype;
+    q->n.assign(n, n + P);
+    q->m.assign(m, m + P);
+    hs = plan_build(q, P);
+    if (hs != HB_OK) {
+        const std::string msg = g_err;
+        hb_plan_destroy(q);
+        g_err = msg;
+        return hs;
+    }
+    *out = q;
+    g_err.clear();
+    return HB_OK;
+}
+
+extern "C" hb_status hb_plan_execute(hb_plan *q, const void *XY, hb_result *res, void *stream)
+{
+    if (!q || !XY || !res) return fail(HB_ERR_INVALID_ARG, "plan, XY and out must be non-NULL");
+    hb_ctx *c = q->c;
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t user = (cudaStream_t)stream;
+    const int64_t P = q->pl.P;
+    cudaPointerAttributes attr{};
+    const cudaError_t ae = cudaPointerGetAttributes(&attr, XY);
+    if (ae != cudaSuccess) cudaGetLastError();
+    const bool on_device = ae == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    const void *src = XY;
+    if (!on_device) {
+        if (!q->xy_dev && cudaMalloc(&q->xy_dev, q->xy_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            q->xy_dev = nullptr;
+            return fail(HB_ERR_OOM, "plan input buffer of %zu bytes", q->xy_bytes);
+        }
+        CK(cudaMemcpyAsync(q->xy_dev, XY, q->xy_bytes, cudaMemcpyHostToDevice, user));
+        src = q->xy_dev;
+    }
+    if (src != q->bound) {
+        for (int64_t p = 0; p < P; ++p) {
+            q->pl.meta[p].X = (const char *)src + (size_t)q->off[p] * q->d * q->esz;
+            q->pl.meta[p].Y = (const char *)q->pl.meta[p].X + (size_t)q->n[p] * q->d * q->esz;
+        }
+        char *h = q->host + q->res_bytes;
+        memcpy(h, q->pl.meta.data(), q->mbytes);
+        CK(cudaMemcpyAsync(q->b.meta, h, q->mbytes, cudaMemcpyHostToDevice, user));
+        q->bound = src;
+    }
+    CK(cudaGraphLaunch(q->exec, user));
+    CK(cudaStreamSynchronize(user));
+    const unsigned int *cnt = (const unsigned int *)q->host;
+    if (cnt[2]) return fail(HB_ERR_TIMEOUT, "a bounded device wait expired in the mixed path");
+    if (cnt[1])  // recheck list outgrew the planned capacity: the unplanned path sizes it anew
+        return hb_perm_test_batched(c, P, XY, q->n.data(), q->m.data(), q->d, q->dtype, &q->opts, res, stream);
+    const PairOut *outp = (const PairOut *)(q->host + 64);
+    hb_status first = HB_OK;
+    for (int64_t p = 0; p < P; ++p) {
+        fill_result(outp[p], &res[p]);
+        if (outp[p].status != HB_OK && first == HB_OK) first = (hb_status)outp[p].status;
+    }
+    c->last_timed = q->timed;
+    if (q->timed)
+        for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], q->tev[k], q->tev[k + 1]);
+    c->last_launches = q->launches;
     if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
     g_err.clear();
     return HB_OK;

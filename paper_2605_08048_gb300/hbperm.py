@@ -82,6 +82,12 @@ def lib():
         L.hb_perm_test_batched.restype = C.c_int
         L.hb_perm_labels.argtypes = [u64, u32, i64, i64, i64, i64, vp, vp]
         L.hb_perm_labels.restype = C.c_int
+        L.hb_plan_create.argtypes = [vp, i64, vp, vp, i64, i32, C.POINTER(hb_opts), C.POINTER(vp)]
+        L.hb_plan_create.restype = C.c_int
+        L.hb_plan_execute.argtypes = [vp, vp, C.POINTER(hb_result), vp]
+        L.hb_plan_execute.restype = C.c_int
+        L.hb_plan_destroy.argtypes = [vp]
+        L.hb_plan_destroy.restype = None
         L.hb_last_error.argtypes = []
         L.hb_last_error.restype = C.c_char_p
         _lib = L
@@ -217,6 +223,44 @@ def hb_perm_test_batched(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, st
     if check:
         _check(st)
     return [r.as_dict() for r in res]
+
+
+class Plan:
+    """hb_plan: a batch shape (sizes n, m, d, dtype, opts) planned once; each
+    execute() replays the captured CUDA graph of the whole test on new data."""
+
+    def __init__(self, ctx: Context, n, m, d: int, dtype, opts: hb_opts):
+        self.P = len(n)
+        self.d = int(d)
+        self.dtype = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
+        na = (C.c_int64 * self.P)(*[int(v) for v in n])
+        ma = (C.c_int64 * self.P)(*[int(v) for v in m])
+        h = C.c_void_p()
+        _check(lib().hb_plan_create(ctx.handle, self.P, na, ma, self.d, self.dtype, C.byref(opts), C.byref(h)))
+        self._h = h
+        self._ctx = ctx  # the plan keeps the context alive
+
+    def execute(self, XY: torch.Tensor, stream=None, check=True):
+        if not XY.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        if XY.shape[1] != self.d or _dtype_code(XY) != self.dtype:
+            raise ValueError("XY does not match the plan's d / dtype")
+        res = (hb_result * self.P)()
+        st = lib().hb_plan_execute(self._h, C.c_void_p(XY.data_ptr()), res, _stream(stream))
+        if check:
+            _check(st)
+        return [r.as_dict() for r in res]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hb_perm_labels(seed: int, stream_id: int, n: int, N: int, b0: int, count: int, device=None, stream=None):
