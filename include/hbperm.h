@@ -75,9 +75,19 @@ typedef enum { HB_STAT_LOGVOL_VMF = 0, HB_STAT_ONE_MINUS_R2 = 1, HB_STAT_MEAN_CO
 typedef enum { HB_ALT_TWO_SIDED = 0, HB_ALT_GREATER = 1, HB_ALT_LESS = 2 } hb_alt;
 
 /* HB_PATH_MIXED: exact 16-bit fixed-point slices of Z on tcgen05 tensor
- * cores (BF16 operands, FP32 accumulators in TMEM).  HB_PATH_FP32_PLAIN: the
- * paper's Algorithm 2 taken literally (+-1 signs, FP32 SIMT GEMM). */
-typedef enum { HB_PATH_MIXED = 0, HB_PATH_FP32_PLAIN = 1 } hb_path;
+ * cores (BF16 operands, FP32 accumulators in TMEM), wide column tiles (128
+ * z-columns per accumulator tile; 64 for FP32 input).  HB_PATH_MIXED_NARROW:
+ * the same with half-width column tiles.  HB_PATH_FP32_PLAIN: the paper's
+ * Algorithm 2 taken literally (+-1 signs, FP32 SIMT GEMM).  HB_PATH_AUTO:
+ * each pair takes the route the context's route table holds for its size
+ * (hb_autotune; untuned: HB_PATH_MIXED up to n + m = 65536, the SIMT path
+ * above).  All paths give identical results. */
+typedef enum {
+    HB_PATH_MIXED = 0,
+    HB_PATH_FP32_PLAIN = 1,
+    HB_PATH_AUTO = 2,
+    HB_PATH_MIXED_NARROW = 3
+} hb_path;
 
 typedef struct {
     uint64_t seed;        /* Philox key (key0 = low 32 bits, key1 = high 32 bits)           */
@@ -165,6 +175,25 @@ hb_status hb_plan_execute(hb_plan *plan, const void *XY, hb_result *out, void *s
 
 /* Frees the plan's graph, streams, workspace and staging (NULL is a no-op). */
 void hb_plan_destroy(hb_plan *plan);
+
+/* Route tuning (the paper's Sec. 3.2 leaves the block size and the GEMM
+ * route to the implementation; none of them changes a result).  Pair sizes
+ * N = n + m fall into HB_ROUTE_BUCKETS buckets: bucket 0 holds N <= 64,
+ * bucket k holds 2^(k+5) < N <= 2^(k+6).  hb_autotune times, for every
+ * bucket up to min(max_N, 65536), a synthetic batch of about 2^18 rows of
+ * d unit-norm values of `dtype` (pairs of size 2^(k+6), split evenly) with
+ * min(opts->B, 1023) relabellings on HB_PATH_MIXED, HB_PATH_MIXED_NARROW and
+ * HB_PATH_FP32_PLAIN, and stores the fastest in the context's route table,
+ * which HB_PATH_AUTO then follows; buckets above 65536 always take the SIMT
+ * path.  ms_out (host, nullable) receives [HB_ROUTE_BUCKETS][3] wall-clock
+ * milliseconds in that path order, -1 where not timed.  The other fields of
+ * opts (stat, alt, align, seed) are those of the timed runs.  Synchronous;
+ * allocates and frees its own device buffer. */
+#define HB_ROUTE_BUCKETS 15
+hb_status hb_autotune(hb_ctx *ctx, int64_t d, int32_t dtype, const hb_opts *opts, int64_t max_N, float *ms_out);
+
+/* The path (hb_path, never HB_PATH_AUTO) HB_PATH_AUTO gives a pair of size N. */
+hb_status hb_route(hb_ctx *ctx, int64_t N, int32_t *path_out);
 
 /* HB-LABEL-v1 label rows for relabellings b0 .. b0+count-1 of a pool of N
  * with group-1 size n (Sec. 3.2: the sign matrix S with exactly n entries

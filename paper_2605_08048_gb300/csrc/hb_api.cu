@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -73,6 +74,9 @@ struct hb_ctx {
     // kernels leave free instead of holding them back.
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, enter = nullptr, leave = nullptr;
+    // route table of HB_PATH_AUTO, per size bucket (hb_autotune)
+    int32_t route[HB_ROUTE_BUCKETS];
+    bool tuned = false;
     // relabelling statistics of hb_null_quantiles
     void *tbuf = nullptr;
     size_t tbuf_cap = 0;
@@ -94,6 +98,7 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
     CK(cudaSetDevice(device));
     hb_ctx *c = new hb_ctx();
     c->device = device;
+    for (int k = 0; k < HB_ROUTE_BUCKETS; ++k) c->route[k] = k <= 10 ? HB_PATH_MIXED : HB_PATH_FP32_PLAIN;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     int prio_least = 0, prio_greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
@@ -229,7 +234,7 @@ static hb_status validate_opts(const hb_opts *op)
     if (op->alt < 0 || op->alt > 2) return fail(HB_ERR_INVALID_ARG, "alt %d unknown", op->alt);
     if (op->reflect_side != 0 && op->reflect_side != 1)
         return fail(HB_ERR_INVALID_ARG, "reflect_side %d unknown", op->reflect_side);
-    if (op->path != HB_PATH_MIXED && op->path != HB_PATH_FP32_PLAIN)
+    if (op->path < HB_PATH_MIXED || op->path > HB_PATH_MIXED_NARROW)
         return fail(HB_ERR_INVALID_ARG, "path %d unknown", op->path);
     if (!op->exhaustive && (op->B < 1 || op->B > 0x7fffffffLL))
         return fail(HB_ERR_INVALID_ARG, "B = %lld outside [1, 2^31)", (long long)op->B);
@@ -237,6 +242,37 @@ static hb_status validate_opts(const hb_opts *op)
 }
 
 // Builds the per-pair metadata.  X/Y pointers filled by the caller.
+// size bucket of a pair: 0 for N <= 64, k for 2^(k+5) < N <= 2^(k+6)
+static int route_bucket(int64_t N)
+{
+    int k = 0;
+    while (k < HB_ROUTE_BUCKETS - 1 && ((int64_t)64 << k) < N) ++k;
+    return k;
+}
+
+static int32_t route_for(const hb_ctx *c, int64_t N)
+{
+    if (N > 65536) return HB_PATH_FP32_PLAIN;  // the only route for large pairs
+    return c->route[route_bucket(N)];
+}
+
+// One route for a whole batch under HB_PATH_AUTO (plans and the triage calls):
+// the SIMT path if any pair needs it, else the route of the bucket holding
+// most of the batch's rows.
+static int32_t route_for_batch(const hb_ctx *c, int64_t P, const int64_t *n, const int64_t *m)
+{
+    int64_t rows[4] = {0, 0, 0, 0};
+    for (int64_t p = 0; p < P; ++p) {
+        const int32_t r = route_for(c, n[p] + m[p]);
+        if (r == HB_PATH_FP32_PLAIN && n[p] + m[p] > 65536) return HB_PATH_FP32_PLAIN;
+        rows[r] += n[p] + m[p];
+    }
+    int32_t best = HB_PATH_MIXED;
+    for (int32_t r = 0; r < 4; ++r)
+        if (r != HB_PATH_AUTO && rows[r] > rows[best]) best = r;
+    return best;
+}
+
 static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
                            const hb_opts &op, bool align_only, bool want_T)
 {
@@ -250,13 +286,16 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
     o.align = op.align ? 1 : 0;
     o.reflect_side = op.reflect_side;
     o.exhaustive = op.exhaustive ? 1 : 0;
-    o.path = align_only ? 1 : op.path;
+    // HB_PATH_AUTO is resolved by the caller; the narrow tensor-core route is
+    // the mixed path with half-width column tiles
+    const bool narrow = op.path == HB_PATH_MIXED_NARROW;
+    o.path = align_only ? 1 : (narrow ? HB_PATH_MIXED : op.path);
     o.d = (int)d;
     o.dtype = dtype;
     o.want_T = want_T ? 1 : 0;
     if (o.path == HB_PATH_MIXED) {
         o.slices = dtype == HB_F32 ? 3 : 2;
-        o.cw = o.slices == 2 ? 128 : 64;
+        o.cw = (o.slices == 2 ? 128 : 64) >> (narrow ? 1 : 0);
         o.d_pad = (int)rup(d, o.cw);
     } else {
         o.slices = 0;
@@ -695,8 +734,10 @@ extern "C" hb_status hb_perm_test(hb_ctx *c, const void *X, int64_t n, const voi
         return fail(HB_ERR_DEGENERATE, "n = %lld and m = %lld must both be >= 2", (long long)n, (long long)m);
     }
     CK(cudaSetDevice(c->device));
+    hb_opts op = *opts;
+    if (op.path == HB_PATH_AUTO) op.path = route_for(c, n + m);
     Plan pl;
-    hs = make_plan(pl, 1, &n, &m, d, dtype, *opts, false, T_out != nullptr);
+    hs = make_plan(pl, 1, &n, &m, d, dtype, op, false, T_out != nullptr);
     if (hs != HB_OK) return hs;
     pl.meta[0].X = X;
     pl.meta[0].Y = Y;
@@ -705,6 +746,69 @@ extern "C" hb_status hb_perm_test(hb_ctx *c, const void *X, int64_t n, const voi
     if (hs != HB_OK) return hs;
     fill_result(out[0], res);
     if (out[0].status != HB_OK) return fail((hb_status)out[0].status, "test failed with status %d", out[0].status);
+    g_err.clear();
+    return HB_OK;
+}
+
+// HB_PATH_AUTO over pairs that take different routes: one run per route on
+// the pairs of that route (XY staged on the device once if it is host memory).
+static hb_status batched_routes(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m, int64_t d,
+                                int32_t dtype, hb_opts op, const std::vector<int64_t> (&sel)[4], hb_result *res,
+                                cudaStream_t s)
+{
+    const size_t esz = dtype == HB_F32 ? 4 : 2;
+    std::vector<int64_t> off(P + 1, 0);
+    for (int64_t p = 0; p < P; ++p) off[p + 1] = off[p] + n[p] + m[p];
+    const size_t xy_bytes = (size_t)off[P] * d * esz;
+    cudaPointerAttributes attr{};
+    const cudaError_t ae = cudaPointerGetAttributes(&attr, XY);
+    if (ae != cudaSuccess) cudaGetLastError();
+    const bool on_device = ae == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    void *tmp = nullptr;
+    const char *base = (const char *)XY;
+    if (!on_device) {
+        if (cudaMalloc(&tmp, xy_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HB_ERR_OOM, "device copy of the input (%zu bytes)", xy_bytes);
+        }
+        if (cudaMemcpyAsync(tmp, XY, xy_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaFree(tmp);
+            return fail(HB_ERR_CUDA, "copy of the input failed");
+        }
+        base = (const char *)tmp;
+    }
+    hb_status hs = HB_OK, first = HB_OK;
+    for (int r = 0; r < 4 && hs == HB_OK; ++r) {
+        const std::vector<int64_t> &ix = sel[r];
+        if (ix.empty()) continue;
+        const int64_t S = (int64_t)ix.size();
+        std::vector<int64_t> ns(S), ms(S);
+        for (int64_t i = 0; i < S; ++i) {
+            ns[i] = n[ix[i]];
+            ms[i] = m[ix[i]];
+        }
+        op.path = r;
+        Plan pl;
+        hs = make_plan(pl, S, ns.data(), ms.data(), d, dtype, op, false, false);
+        if (hs != HB_OK) break;
+        for (int64_t i = 0; i < S; ++i) {
+            pl.meta[i].X = base + (size_t)off[ix[i]] * d * esz;
+            pl.meta[i].Y = (const char *)pl.meta[i].X + (size_t)ns[i] * d * esz;
+        }
+        std::vector<PairOut> out;
+        hs = run(c, pl, nullptr, 0, nullptr, false, nullptr, nullptr, nullptr, nullptr, s, out);
+        if (hs != HB_OK) break;
+        for (int64_t i = 0; i < S; ++i) {
+            fill_result(out[i], &res[ix[i]]);
+            if (out[i].status != HB_OK && first == HB_OK) first = (hb_status)out[i].status;
+        }
+    }
+    if (tmp) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+    }
+    if (hs != HB_OK) return hs;
+    if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
     g_err.clear();
     return HB_OK;
 }
@@ -720,8 +824,21 @@ extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, 
     hs = validate_opts(opts);
     if (hs != HB_OK) return hs;
     CK(cudaSetDevice(c->device));
+    hb_opts op = *opts;
+    if (op.path == HB_PATH_AUTO) {
+        std::vector<int64_t> sel[4];
+        for (int64_t p = 0; p < P; ++p) sel[route_for(c, n[p] + m[p])].push_back(p);
+        int used = 0, only = HB_PATH_MIXED;
+        for (int r = 0; r < 4; ++r)
+            if (!sel[r].empty()) {
+                ++used;
+                only = r;
+            }
+        if (used > 1) return batched_routes(c, P, XY, n, m, d, dtype, op, sel, res, (cudaStream_t)stream);
+        op.path = only;
+    }
     Plan pl;
-    hs = make_plan(pl, P, n, m, d, dtype, *opts, false, false);
+    hs = make_plan(pl, P, n, m, d, dtype, op, false, false);
     if (hs != HB_OK) return hs;
     const size_t esz = dtype == HB_F32 ? 4 : 2;
     std::vector<int64_t> off(P + 1, 0);
@@ -891,6 +1008,7 @@ extern "C" hb_status hb_plan_create(hb_ctx *c, int64_t P, const int64_t *n, cons
     q->dtype = dtype;
     q->n.assign(n, n + P);
     q->m.assign(m, m + P);
+    if (q->opts.path == HB_PATH_AUTO) q->opts.path = route_for_batch(c, P, n, m);
     hs = plan_build(q, P);
     if (hs != HB_OK) {
         const std::string msg = g_err;
@@ -955,6 +1073,107 @@ extern "C" hb_status hb_plan_execute(hb_plan *q, const void *XY, hb_result *res,
     return HB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// route tuning
+// ---------------------------------------------------------------------------
+// Synthetic unit-norm rows for timing the routes: entry j of row r is a
+// Philox uniform in [-1/2, 1/2) (counter (j, r, 0x7D5E, 0), key (seed, 0)),
+// plus 0.3 on coordinate 0 (a common mean direction); the row is normalised
+// in FP32 and stored as dtype (BF16 round-to-nearest-even).
+__global__ void k_tune_rows(void *out, int64_t rows, int d, int dtype, uint32_t seed)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    auto val = [&](int j) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)r, 0x7D5Eu, 0u), seed, 0u);
+        return (float)(w.x >> 8) * (1.0f / 16777216.0f) - 0.5f + (j == 0 ? 0.3f : 0.0f);
+    };
+    float ss = 0.f;
+    for (int j = 0; j < d; ++j) {
+        const float v = val(j);
+        ss = fmaf(v, v, ss);
+    }
+    const float inv = 1.0f / sqrtf(ss);
+    for (int j = 0; j < d; ++j) {
+        const float v = val(j) * inv;
+        if (dtype == HB_F32) {
+            reinterpret_cast<float *>(out)[r * d + j] = v;
+        } else {
+            uint32_t u = __float_as_uint(v);
+            u += 0x7FFFu + ((u >> 16) & 1u);
+            reinterpret_cast<unsigned short *>(out)[r * d + j] = (unsigned short)(u >> 16);
+        }
+    }
+}
+
+extern "C" hb_status hb_route(hb_ctx *c, int64_t N, int32_t *path_out)
+{
+    if (!c || !path_out) return fail(HB_ERR_INVALID_ARG, "ctx and path_out must be non-NULL");
+    if (N < 2 || N > (1 << 20)) return fail(HB_ERR_INVALID_ARG, "N = %lld outside [2, 2^20]", (long long)N);
+    *path_out = route_for(c, N);
+    g_err.clear();
+    return HB_OK;
+}
+
+extern "C" hb_status hb_autotune(hb_ctx *c, int64_t d, int32_t dtype, const hb_opts *opts, int64_t max_N,
+                                 float *ms_out)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    if (opts->exhaustive) return fail(HB_ERR_INVALID_ARG, "route tuning needs sampled relabellings");
+    CK(cudaSetDevice(c->device));
+    constexpr int NR = 3;
+    const int32_t paths[NR] = {HB_PATH_MIXED, HB_PATH_MIXED_NARROW, HB_PATH_FP32_PLAIN};
+    if (ms_out)
+        for (int k = 0; k < HB_ROUTE_BUCKETS * NR; ++k) ms_out[k] = -1.0f;
+    const int64_t rows = (int64_t)1 << 18;
+    const size_t esz = dtype == HB_F32 ? 4 : 2;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)rows * d * esz) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HB_ERR_OOM, "tuning buffer of %zu bytes", (size_t)rows * d * esz);
+    }
+    cudaStream_t s = nullptr;
+    k_tune_rows<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(buf, rows, (int)d, dtype, 0x5EEDu);
+    hs = cudaGetLastError() == cudaSuccess ? HB_OK : fail(HB_ERR_CUDA, "tuning data kernel failed");
+    hb_opts op = *opts;
+    op.B = std::min<int64_t>(opts->B, 1023);
+    const int64_t top = std::min<int64_t>(std::max<int64_t>(max_N, 64), 65536);
+    std::vector<hb_result> res;
+    for (int k = 0; hs == HB_OK && k < HB_ROUTE_BUCKETS && ((int64_t)64 << k) <= top; ++k) {
+        const int64_t N = (int64_t)64 << k, P = std::max<int64_t>(1, rows / N);
+        std::vector<int64_t> n(P, N / 2), m(P, N - N / 2);
+        res.assign(P, hb_result{});
+        float best = 0.f;
+        int32_t best_path = HB_PATH_MIXED;
+        for (int r = 0; r < NR && hs == HB_OK; ++r) {
+            op.path = paths[r];
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && hs == HB_OK; ++rep) {  // the second run is timed
+                const auto t0 = std::chrono::steady_clock::now();
+                hs = hb_perm_test_batched(c, P, buf, n.data(), m.data(), d, dtype, &op, res.data(), s);
+                ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
+            if (hs != HB_OK) break;
+            if (ms_out) ms_out[k * NR + r] = ms;
+            if (r == 0 || ms < best) {
+                best = ms;
+                best_path = paths[r];
+            }
+        }
+        if (hs == HB_OK) c->route[k] = best_path;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (hs != HB_OK) return hs;
+    c->tuned = true;
+    g_err.clear();
+    return HB_OK;
+}
+
 extern "C" hb_status hb_ctx_set_timing(hb_ctx *c, int32_t enable)
 {
     if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
@@ -993,6 +1212,7 @@ static hb_status batched_common(hb_ctx *c, int64_t P, const void *XY, const int6
     if (hs != HB_OK) return hs;
     CK(cudaSetDevice(c->device));
     hb_opts op = *opts;
+    if (op.path == HB_PATH_AUTO) op.path = route_for_batch(c, P, n, m);
     if (features) {
         op.path = HB_PATH_FP32_PLAIN;  // no slices needed
         op.B = 1;

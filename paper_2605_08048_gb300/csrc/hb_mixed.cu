@@ -242,11 +242,13 @@ __device__ __forceinline__ uint32_t expand2(uint32_t b)
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int S>
+template <int S, int CW>
 __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
-    constexpr int CW = (S == 2) ? 128 : 64;  // z-columns per column tile
-    constexpr int NACC = S * CW;             // accumulator columns (256 or 192)
+    // CW z-columns per column tile: 128 (wide) or 64 (narrow) for two slices,
+    // 64 or 32 for three
+    constexpr int NACC = S * CW;  // accumulator columns of one buffer
+    static_assert(NACC <= 256 && CW % 32 == 0 && NACC % 16 == 0, "column tile");
     constexpr uint32_t B_BYTES = (uint32_t)NACC * 128u;
 
     extern __shared__ uint8_t smem_raw[];
@@ -582,7 +584,7 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     }
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode(err);
     if (!enc) return cudaErrorNotSupported;
-    const int nacc = S == 2 ? 256 : 192;
+    const int nacc = S * a.o.cw;
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)a.zq_ld, (cuuint64_t)a.zq_rows};
     const cuuint64_t gstride[1] = {(cuuint64_t)a.zq_ld * 2};
@@ -609,7 +611,13 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     prm.overflow = a.overflow;
     prm.timeout = a.timeout;
     prm.T_out = a.T_out;
-    void (*kern)(const CUtensorMap, const MixedParams) = (S == 2) ? k_mixed<2> : k_mixed<3>;
+    void (*kern)(const CUtensorMap, const MixedParams) = nullptr;
+    if (S == 2) kern = a.o.cw == 128 ? k_mixed<2, 128> : a.o.cw == 64 ? k_mixed<2, 64> : nullptr;
+    else kern = a.o.cw == 64 ? k_mixed<3, 64> : a.o.cw == 32 ? k_mixed<3, 32> : nullptr;
+    if (!kern) {
+        err = "unsupported column tile width";
+        return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

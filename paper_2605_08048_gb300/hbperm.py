@@ -18,7 +18,8 @@ HB_OK, HB_ERR_INVALID_ARG, HB_ERR_DEGENERATE, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TI
 HB_F32, HB_BF16 = 0, 1
 HB_STAT_LOGVOL_VMF, HB_STAT_ONE_MINUS_R2, HB_STAT_MEAN_COSDIST = 0, 1, 2
 HB_ALT_TWO_SIDED, HB_ALT_GREATER, HB_ALT_LESS = 0, 1, 2
-HB_PATH_MIXED, HB_PATH_FP32_PLAIN = 0, 1
+HB_PATH_MIXED, HB_PATH_FP32_PLAIN, HB_PATH_AUTO, HB_PATH_MIXED_NARROW = 0, 1, 2, 3
+ROUTE_BUCKETS = 15  # size buckets of the route table (hb_autotune)
 
 
 class HbError(RuntimeError):
@@ -88,6 +89,10 @@ def lib():
         L.hb_plan_execute.restype = C.c_int
         L.hb_plan_destroy.argtypes = [vp]
         L.hb_plan_destroy.restype = None
+        L.hb_autotune.argtypes = [vp, i64, i32, C.POINTER(hb_opts), i64, C.POINTER(C.c_float)]
+        L.hb_autotune.restype = C.c_int
+        L.hb_route.argtypes = [vp, i64, C.POINTER(i32)]
+        L.hb_route.restype = C.c_int
         L.hb_last_error.argtypes = []
         L.hb_last_error.restype = C.c_char_p
         _lib = L
@@ -261,6 +266,25 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def autotune(ctx: Context, d: int, dtype, opts: hb_opts, max_N: int = 65536):
+    """Times the three routes per size bucket and fills the context's route
+    table; returns the [ROUTE_BUCKETS][3] wall-clock ms (MIXED, MIXED_NARROW,
+    FP32_PLAIN; -1 = not timed) as a numpy array."""
+    import numpy as np
+
+    code = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
+    ms = (C.c_float * (ROUTE_BUCKETS * 3))()
+    _check(lib().hb_autotune(ctx.handle, int(d), code, C.byref(opts), int(max_N), ms))
+    return np.array(ms[:], dtype=np.float32).reshape(ROUTE_BUCKETS, 3)
+
+
+def route(ctx: Context, N: int) -> int:
+    """The path HB_PATH_AUTO takes for a pair of size N."""
+    r = C.c_int32()
+    _check(lib().hb_route(ctx.handle, int(N), C.byref(r)))
+    return r.value
 
 
 def hb_perm_labels(seed: int, stream_id: int, n: int, N: int, b0: int, count: int, device=None, stream=None):
