@@ -32,6 +32,13 @@ if ROOT not in sys.path:
 
 METRIC = "perm-tests/sec (B=9999, d=768) vs plain FP32 GPU at exact p-count; % roofline"
 UNIT = "pair-tests/s"
+# DRAM bytes (read + write) of one group-sum GEMM launch per input token of
+# this workload (B = 9999, d = 768), from the ncu capture of the 256-pair case
+# (238,932 tokens: 1,159,872,024 bytes; profiles/k_mixed_batched256_d768.md).
+# Traffic grows with the tokens, so a launch moves this figure x sum(N).  It
+# describes the kernel source it was measured on: another hb_mixed.cu reports
+# null until it is captured again.
+MIXED_TRAFFIC = {"source_sha256_prefix": "9a9ee521c53b5a5f", "bytes_per_token": 1159872024.0 / 238932}
 WORKLOAD = ("batched: 4096 word pairs, n and m lognormal (median 300, sigma_log 1.0, clipped 20..8000), d=768 "
             "BF16, half null (sigma 0.35, random directions) / half alternative (sigma ratio 1.1), B=9999 each, "
             "Householder-aligned, two-sided log-volume statistic")
@@ -240,6 +247,13 @@ def main():
     achieved = algo_flops / (gemm_ms / 1000.0) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", 1700.0))
     traffic = None
+    if path == H.HB_PATH_MIXED and a.B == 9999 and a.d == 768:
+        import hashlib
+
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2605_08048_gb300", "csrc", "hb_mixed.cu")
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest().startswith(MIXED_TRAFFIC["source_sha256_prefix"]):
+                traffic = MIXED_TRAFFIC["bytes_per_token"] * float(np.sum(n + m))
     stage_ms = {k: round(statistics.mean(s[k] for s in stages), 3) for k in stages[0]}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
