@@ -242,7 +242,7 @@ def main():
 
     # roofline of the dominant kernel (group-sum GEMM + fused epilogue)
     pk, pk_kind = peaks()
-    gemm_ms = statistics.mean(s["gemm_epilogue"] for s in stages)
+    gemm_ms = statistics.mean(s["gemm_kernels"] for s in stages)  # the GEMM launches' own durations
     algo_flops = 2.0 * a.B * float(np.sum(n + m)) * a.d  # Eq. gemm: 2 B N d per pair, one launch per step
     achieved = algo_flops / (gemm_ms / 1000.0) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", 1700.0))

@@ -290,10 +290,12 @@ hb_status hb_triage_predict_p(int64_t P, const float *quant, const double *tobs,
 hb_status hb_ctx_set_timing(hb_ctx *ctx, int32_t enable);
 
 /* Stage durations of the last hb_perm_test / hb_perm_test_batched call on
- * this context, in milliseconds (ms_out, host, 6 floats): [0] alignment
+ * this context, in milliseconds (ms_out, host, 7 floats): [0] alignment
  * (column sums, axis, reflection), [1] Z statistics, fixed-point slices and
- * T_obs, [2] label draws, [3] group-sum GEMM with the fused statistic
- * epilogue, [4] exact recheck, [5] p-values and the result copy.
+ * T_obs, [2] label draws not hidden behind steps 1-4, [3] group-sum GEMM
+ * with the fused statistic epilogue, including waits for label chunks still
+ * being drawn, [4] exact recheck, [5] p-values and the result copy, [6] the
+ * sum of the GEMM launches' own durations.
  * n_launches (host, nullable) receives the kernel launches of that call.
  * HB_ERR_INVALID_ARG if timing was not enabled for that call. */
 hb_status hb_ctx_stage_times(hb_ctx *ctx, float *ms_out, int32_t *n_launches);

@@ -53,6 +53,10 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+namespace {
+constexpr int LABEL_CHUNKS = 4;  // label-draw chunks of a mixed-path call
+}
+
 struct hb_ctx {
     int device = 0;
     int sms = 0;
@@ -66,7 +70,8 @@ struct hb_ctx {
     bool timing = false;
     bool last_timed = false;
     cudaEvent_t tev[7] = {};
-    float last_ms[6] = {};
+    cudaEvent_t gev[2 * LABEL_CHUNKS] = {};  // around each GEMM launch
+    float last_ms[7] = {};
     int last_launches = 0;
     // Streams of a call: the caller's stream forks into `main` (highest
     // priority) and joins back at the end; the label draws, which depend on no
@@ -74,6 +79,7 @@ struct hb_ctx {
     // kernels leave free instead of holding them back.
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, enter = nullptr, leave = nullptr;
+    cudaEvent_t lab_ev[LABEL_CHUNKS] = {};  // label chunk c drawn
     // route table of HB_PATH_AUTO, per size bucket (hb_autotune)
     int32_t route[HB_ROUTE_BUCKETS];
     bool tuned = false;
@@ -83,6 +89,13 @@ struct hb_ctx {
 };
 
 extern "C" void hb_ctx_destroy(hb_ctx *c);
+
+static bool create_events(cudaEvent_t *ev, int n)
+{
+    for (int k = 0; k < n; ++k)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
 
 static void mark(hb_ctx *c, int k, cudaStream_t s)
 {
@@ -108,6 +121,7 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
         cudaEventCreateWithFlags(&c->enter, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->leave, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->main, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        !create_events(c->lab_ev, LABEL_CHUNKS) ||
         cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess) {
         hb_ctx_destroy(c);
         return fail(HB_ERR_CUDA, "stream or event creation failed");
@@ -127,12 +141,16 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
     }
     for (int k = 0; k < 7; ++k)
         if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+    for (cudaEvent_t e : c->gev)
+        if (e) cudaEventDestroy(e);
     for (cudaStream_t q : {c->main, c->side})
         if (q) {
             cudaStreamSynchronize(q);
             cudaStreamDestroy(q);
         }
     for (cudaEvent_t e : {c->fork, c->join, c->enter, c->leave})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->lab_ev)
         if (e) cudaEventDestroy(e);
     if (c->tbuf) cudaFree(c->tbuf);
     if (c->ws) cudaFree(c->ws);
@@ -218,6 +236,14 @@ struct Plan {
     std::vector<WorkItem> items;  // (pair, 128-relabelling tile), costliest pairs first
     int64_t total_rows_pad = 0, total_label_words = 0, total_B = 0;
     int max_Bpad = 0, max_W = 0, max_N = 0;
+    // mixed path: pairs in the items' order, cut into nlc chunks of about
+    // equal label work; chunk c is pairs order[lc_pair[c] .. lc_pair[c+1]) and
+    // items [lc_item[c], lc_item[c+1]), so its GEMM can start as soon as its
+    // labels are drawn while the next chunk's labels are still being drawn
+    std::vector<int> order;
+    int nlc = 0;
+    int lc_pair[LABEL_CHUNKS + 1] = {};
+    int lc_item[LABEL_CHUNKS + 1] = {};
 };
 
 static hb_status validate_common(int64_t d, int32_t dtype)
@@ -358,6 +384,37 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int p : order)
             if (pl.init_bad[p] == 0)
                 for (int g = 0; g < pl.meta[p].B_pad / (128 * MIXED_CLUSTER); ++g) pl.items.push_back(WorkItem{p, g});
+        // label chunks of about equal label work, in the same order
+        pl.order = order;
+        int64_t total = 0;
+        for (int p : order) total += (int64_t)pl.meta[p].W * pl.meta[p].B_pad;
+        int cuts[LABEL_CHUNKS + 1];
+        cuts[0] = 0;
+        int64_t acc = 0;
+        int i = 0;
+        for (int c = 1; c < LABEL_CHUNKS; ++c) {
+            const int64_t target = total * c / LABEL_CHUNKS;
+            while (i < (int)P && acc < target) {
+                acc += (int64_t)pl.meta[order[i]].W * pl.meta[order[i]].B_pad;
+                ++i;
+            }
+            cuts[c] = i;
+        }
+        cuts[LABEL_CHUNKS] = (int)P;
+        pl.nlc = 0;
+        pl.lc_pair[0] = 0;
+        for (int c = 1; c <= LABEL_CHUNKS; ++c)
+            if (cuts[c] > pl.lc_pair[pl.nlc]) pl.lc_pair[++pl.nlc] = cuts[c];
+        // item boundaries: items follow `order`, so count the items of each chunk's pairs
+        int it = 0;
+        pl.lc_item[0] = 0;
+        for (int c = 0; c < pl.nlc; ++c) {
+            for (int k = pl.lc_pair[c]; k < pl.lc_pair[c + 1]; ++k) {
+                const int p = order[k];
+                if (pl.init_bad[p] == 0) it += pl.meta[p].B_pad / (128 * MIXED_CLUSTER);
+            }
+            pl.lc_item[c + 1] = it;
+        }
     }
     return HB_OK;
 }
@@ -384,6 +441,7 @@ struct Bufs {
     PairOut *out;
     void *xy;
     WorkItem *items;
+    int *order;  // mixed path: pairs in the items' order
     float *lam;  // Ritz values [P][16] (features mode)
 };
 
@@ -418,6 +476,7 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
         b.scratch = cv.take<double>((size_t)rgrid * 2 * d);
         b.out = cv.take<PairOut>(P);
         b.items = pl.o.path == HB_PATH_MIXED ? cv.take<WorkItem>(pl.items.size()) : nullptr;
+        b.order = pl.o.path == HB_PATH_MIXED ? cv.take<int>(pl.order.size()) : nullptr;
         b.lam = cv.take<float>((size_t)P * 16);
     }
     return cv.off;
@@ -439,7 +498,43 @@ struct Exec {
     cudaEvent_t *tev;        // 7 stage events, or nullptr
     int sms;
     bool capture = false;    // enqueued under stream capture (events become graph nodes)
+    cudaEvent_t *lab_ev = nullptr;  // LABEL_CHUNKS events: label chunk c drawn (mixed path)
+    cudaEvent_t *gev = nullptr;     // 2 * LABEL_CHUNKS timing events around the GEMM launches, or nullptr
 };
+
+static void xrec(const Exec &ex, cudaEvent_t e)
+{
+    cudaEventRecordWithFlags(e, ex.s, ex.capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// Sum of the GEMM launch durations of the last call (the stage above also
+// holds the waits for later label chunks).
+static float gemm_ms(const Plan &pl, const cudaEvent_t *gev)
+{
+    float total = 0.f;
+    for (int c = 0; c < std::max(pl.nlc, 1); ++c) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, gev[2 * c], gev[2 * c + 1]) == cudaSuccess) total += ms;
+        else cudaGetLastError();  // not recorded: leave no sticky error for the next call
+    }
+    return total;
+}
+
+// Kernel launches of one test call: colsum (2) + axis + reflect + zstats (2) +
+// tobs + label draws + GEMM + recheck (2 per batch) + finalize.
+static int launch_count(const Plan &pl, unsigned int cap, int rgrid)
+{
+    const bool mixed = pl.o.path == HB_PATH_MIXED;
+    const int pchunks = (pl.P + 65534) / 65535;
+    int labels = pchunks, gemm = pchunks;
+    if (mixed) {
+        labels = 0;
+        for (int c = 0; c < pl.nlc; ++c) labels += (pl.lc_pair[c + 1] - pl.lc_pair[c] + 65534) / 65535;
+        gemm = 0;
+        for (int c = 0; c < pl.nlc; ++c) gemm += pl.lc_item[c + 1] > pl.lc_item[c] ? 1 : 0;
+    }
+    return 8 + labels + gemm + 2 * (int)((cap + rgrid - 1) / rgrid);
+}
 
 static void xmark(const Exec &ex, int k)
 {
@@ -461,11 +556,21 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     const RunOpts &o = pl.o;
     const int d = o.d;
     const bool mixed = o.path == HB_PATH_MIXED;
+    const bool chunked = mixed && !features && pl.nlc > 0;
     if (!features) {
-        // labels on the side stream from here on, concurrently with steps 1-4
+        // labels on the side stream from here on, concurrently with steps 1-4 and,
+        // chunk by chunk, with the GEMM of the chunks drawn before
         CK(cudaEventRecord(ex.fork, s));
         CK(cudaStreamWaitEvent(ex.side, ex.fork, 0));
-        launch_labels_pipeline(b.meta, b.st, P, pl.max_Bpad, o, b.bits, ex.side);
+        if (chunked) {
+            for (int c = 0; c < pl.nlc; ++c) {
+                launch_labels_pipeline(b.meta, b.st, b.order, pl.lc_pair[c], pl.lc_pair[c + 1], pl.max_Bpad, o, b.bits,
+                                       ex.side);
+                CK(cudaEventRecord(ex.lab_ev[c], ex.side));
+            }
+        } else {
+            launch_labels_pipeline(b.meta, b.st, nullptr, 0, P, pl.max_Bpad, o, b.bits, ex.side);
+        }
         CK(cudaEventRecord(ex.join, ex.side));
     }
     if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
@@ -498,7 +603,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     } else {
         // step 5: labels, group sums + statistic + band, exact recheck
         xmark(ex, 2);
-        CK(cudaStreamWaitEvent(s, ex.join, 0));  // the "labels" stage is the part not hidden
+        CK(cudaStreamWaitEvent(s, chunked ? ex.lab_ev[0] : ex.join, 0));  // the "labels" stage: the part not hidden
         xmark(ex, 3);
         CK(cudaGetLastError());
         if (mixed) {
@@ -518,19 +623,27 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
             ma.overflow = b.counters + 1;
             ma.timeout = b.counters + 2;
             ma.T_out = T_out;
-            ma.items = b.items;
-            ma.n_work = (int)pl.items.size();
             ma.sms = ex.sms;
-            std::string err;
-            const cudaError_t e = launch_mixed(ma, s, err);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
-                            "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
+            for (int c = 0; c < std::max(pl.nlc, 1); ++c) {
+                if (c > 0) CK(cudaStreamWaitEvent(s, ex.lab_ev[c], 0));
+                ma.items = b.items + (pl.nlc ? pl.lc_item[c] : 0);
+                ma.n_work = pl.nlc ? pl.lc_item[c + 1] - pl.lc_item[c] : (int)pl.items.size();
+                std::string err;
+                if (ex.gev) xrec(ex, ex.gev[2 * c]);
+                const cudaError_t e = launch_mixed(ma, s, err);
+                if (ex.gev) xrec(ex, ex.gev[2 * c + 1]);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
+                                "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
+                }
             }
+            CK(cudaStreamWaitEvent(s, ex.join, 0));  // every side-stream launch joined
         } else {
+            if (ex.gev) xrec(ex, ex.gev[0]);
             launch_plain(b.meta, P, pl.max_Bpad, o, b.st, Z, b.cc, b.bits, b.list, b.counters, cap, b.counters + 1,
                          T_out, s);
+            if (ex.gev) xrec(ex, ex.gev[1]);
         }
         CK(cudaGetLastError());
         xmark(ex, 4);
@@ -590,8 +703,9 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         }
         // metadata upload through pinned staging
         const size_t mbytes = sizeof(PairMeta) * P, cbytes = sizeof(RowChunk) * pl.chunks.size(),
-                     bbytes = sizeof(int) * P, ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0;
-        hs = ensure_stage(c, std::max(mbytes + cbytes + bbytes + ibytes, sizeof(PairOut) * P) + 64);
+                     bbytes = sizeof(int) * P, ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0,
+                     obytes = mixed ? sizeof(int) * pl.order.size() : 0;
+        hs = ensure_stage(c, std::max(mbytes + cbytes + bbytes + ibytes + obytes, sizeof(PairOut) * P) + 64);
         if (hs != HB_OK) return hs;
         char *hs_ = (char *)c->stage;
         memcpy(hs_, pl.meta.data(), mbytes);
@@ -603,6 +717,10 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         if (ibytes) {
             memcpy(hs_ + mbytes + cbytes + bbytes, pl.items.data(), ibytes);
             CK(cudaMemcpyAsync(b.items, hs_ + mbytes + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, s));
+        }
+        if (obytes) {
+            memcpy(hs_ + mbytes + cbytes + bbytes + ibytes, pl.order.data(), obytes);
+            CK(cudaMemcpyAsync(b.order, hs_ + mbytes + cbytes + bbytes + ibytes, obytes, cudaMemcpyHostToDevice, s));
         }
         CK(cudaEventRecord(c->stage_done, s));
         if (align_only) {
@@ -625,7 +743,9 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             return HB_OK;
         }
         // results come back through the same pinned staging (after the metadata copies)
-        const Exec ex{s, c->side, c->fork, c->join, c->timing ? c->tev : nullptr, c->sms};
+        Exec ex{s, c->side, c->fork, c->join, c->timing ? c->tev : nullptr, c->sms};
+        ex.lab_ev = c->lab_ev;
+        ex.gev = c->timing && !tri ? c->gev : nullptr;
         hs = enqueue_test(ex, pl, b, Z, xy_host, xy_bytes, T_out, tri, cap, rgrid, c->stage);
         if (hs != HB_OK) return hs;
         char *h = (char *)c->stage;
@@ -640,10 +760,9 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         c->last_timed = c->timing;
         if (c->timing) {
             for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], c->tev[k], c->tev[k + 1]);
+            c->last_ms[6] = tri ? 0.f : gemm_ms(pl, c->gev);
         }
-        // colsum (2) + axis + reflect + zstats (2) + tobs + labels + GEMM + recheck (2 per batch) + finalize
-        const int pchunks = (int)((P + 65534) / 65535);
-        c->last_launches = 8 + pchunks + (mixed ? 1 : pchunks) + 2 * (int)((cap + rgrid - 1) / rgrid);
+        c->last_launches = launch_count(pl, cap, rgrid);
         return HB_OK;
     }
     return fail(HB_ERR_CUDA, "recheck list kept overflowing");
@@ -886,7 +1005,9 @@ struct hb_plan {
     const void *bound = nullptr;  // input the uploaded pair pointers refer to
     cudaStream_t cs = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t lab_ev[LABEL_CHUNKS] = {};
     cudaEvent_t tev[7] = {};
+    cudaEvent_t gev[2 * LABEL_CHUNKS] = {};
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -905,7 +1026,11 @@ extern "C" void hb_plan_destroy(hb_plan *q)
         if (st) cudaStreamDestroy(st);
     for (cudaEvent_t e : {q->fork, q->join})
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : q->lab_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : q->tev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : q->gev)
         if (e) cudaEventDestroy(e);
     if (q->ws) cudaFree(q->ws);
     if (q->xy_dev) cudaFree(q->xy_dev);
@@ -940,9 +1065,10 @@ static hb_status plan_build(hb_plan *q, int64_t P)
     carve(cv, q->b, pl, false, true, 0, q->cap, q->rgrid);
     q->mbytes = sizeof(PairMeta) * P;
     const size_t cbytes = sizeof(RowChunk) * pl.chunks.size(), bbytes = sizeof(int) * P,
-                 ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0;
+                 ibytes = mixed ? sizeof(WorkItem) * pl.items.size() : 0,
+                 obytes = mixed ? sizeof(int) * pl.order.size() : 0;
     q->res_bytes = (64 + sizeof(PairOut) * P + 255) & ~(size_t)255;
-    const size_t host_bytes = q->res_bytes + std::max(q->mbytes, cbytes + bbytes + ibytes) + 64;
+    const size_t host_bytes = q->res_bytes + std::max(q->mbytes, cbytes + bbytes + ibytes + obytes) + 64;
     if (cudaMallocHost((void **)&q->host, host_bytes) != cudaSuccess) {
         cudaGetLastError();
         q->host = nullptr;
@@ -955,24 +1081,31 @@ static hb_status plan_build(hb_plan *q, int64_t P)
     CK(cudaStreamCreateWithPriority(&q->side, cudaStreamNonBlocking, prio_least));
     CK(cudaEventCreateWithFlags(&q->fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&q->join, cudaEventDisableTiming));
+    if (!create_events(q->lab_ev, LABEL_CHUNKS)) return fail(HB_ERR_CUDA, "event creation failed");
     q->timed = c->timing;
-    if (q->timed)
+    if (q->timed) {
         for (cudaEvent_t &e : q->tev) CK(cudaEventCreate(&e));
+        for (cudaEvent_t &e : q->gev) CK(cudaEventCreate(&e));
+    }
 
     // the metadata that does not depend on the input address, once
     char *h = q->host + q->res_bytes;
     memcpy(h, pl.chunks.data(), cbytes);
     memcpy(h + cbytes, pl.init_bad.data(), bbytes);
     if (ibytes) memcpy(h + cbytes + bbytes, pl.items.data(), ibytes);
+    if (obytes) memcpy(h + cbytes + bbytes + ibytes, pl.order.data(), obytes);
     CK(cudaMemcpyAsync(q->b.chunks, h, cbytes, cudaMemcpyHostToDevice, q->cs));
     CK(cudaMemcpyAsync(q->b.bad, h + cbytes, bbytes, cudaMemcpyHostToDevice, q->cs));
     if (ibytes) CK(cudaMemcpyAsync(q->b.items, h + cbytes + bbytes, ibytes, cudaMemcpyHostToDevice, q->cs));
+    if (obytes) CK(cudaMemcpyAsync(q->b.order, h + cbytes + bbytes + ibytes, obytes, cudaMemcpyHostToDevice, q->cs));
     CK(cudaStreamSynchronize(q->cs));
 
     // capture every device stage of the call
     CK(cudaStreamBeginCapture(q->cs, cudaStreamCaptureModeRelaxed));
     Exec ex{q->cs, q->side, q->fork, q->join, q->timed ? q->tev : nullptr, c->sms};
     ex.capture = true;
+    ex.lab_ev = q->lab_ev;
+    ex.gev = q->timed ? q->gev : nullptr;
     hs = enqueue_test(ex, pl, q->b, q->b.Z, nullptr, 0, nullptr, nullptr, q->cap, q->rgrid, q->host);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(q->cs, &g);
@@ -983,8 +1116,7 @@ static hb_status plan_build(hb_plan *q, int64_t P)
     if (ce != cudaSuccess || !g) return fail(HB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
     q->graph = g;
     CK(cudaGraphInstantiateWithFlags(&q->exec, g, cudaGraphInstantiateFlagUseNodePriority));
-    const int pchunks = (int)((P + 65534) / 65535);
-    q->launches = 8 + pchunks + (mixed ? 1 : pchunks) + 2 * (int)((q->cap + q->rgrid - 1) / q->rgrid);
+    q->launches = launch_count(pl, q->cap, q->rgrid);
     return HB_OK;
 }
 
@@ -1067,6 +1199,7 @@ extern "C" hb_status hb_plan_execute(hb_plan *q, const void *XY, hb_result *res,
     c->last_timed = q->timed;
     if (q->timed)
         for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], q->tev[k], q->tev[k + 1]);
+    if (q->timed) c->last_ms[6] = gemm_ms(q->pl, q->gev);
     c->last_launches = q->launches;
     if (first != HB_OK) return fail(first, "at least one pair failed (first status %d)", first);
     g_err.clear();
@@ -1180,6 +1313,7 @@ extern "C" hb_status hb_ctx_set_timing(hb_ctx *c, int32_t enable)
     if (enable && !c->tev[0]) {
         CK(cudaSetDevice(c->device));
         for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&c->tev[k]));
+        for (cudaEvent_t &e : c->gev) CK(cudaEventCreate(&e));
     }
     c->timing = enable != 0;
     return HB_OK;
@@ -1189,7 +1323,7 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
 {
     if (!c || !ms_out) return fail(HB_ERR_INVALID_ARG, "ctx and ms_out must be non-NULL");
     if (!c->last_timed) return fail(HB_ERR_INVALID_ARG, "timing was not enabled for the last call");
-    for (int k = 0; k < 6; ++k) ms_out[k] = c->last_ms[k];
+    for (int k = 0; k < 7; ++k) ms_out[k] = c->last_ms[k];
     if (n_launches) *n_launches = c->last_launches;
     return HB_OK;
 }

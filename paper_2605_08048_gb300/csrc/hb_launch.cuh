@@ -22,8 +22,8 @@ void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex
                  const ColConst *cc, PairState *pst, cudaStream_t st);
 void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
                         cudaStream_t st);
-void launch_labels_pipeline(const PairMeta *meta, const PairState *pst, int P, int max_Bpad, const RunOpts &o,
-                            uint32_t *bits, cudaStream_t st);
+void launch_labels_pipeline(const PairMeta *meta, const PairState *pst, const int *order, int p_begin, int p_end,
+                            int max_Bpad, const RunOpts &o, uint32_t *bits, cudaStream_t st);
 void launch_plain(const PairMeta *meta, int P, int max_Bpad, const RunOpts &o, PairState *pst, const void *Z,
                   const ColConst *cc, const uint32_t *bits, RecheckItem *list, unsigned int *n_items,
                   unsigned int cap, unsigned int *overflow, float *T_out, cudaStream_t st);

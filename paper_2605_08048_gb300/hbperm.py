@@ -310,7 +310,7 @@ def set_timing(ctx: Context, enable: bool = True):
     _check(L.hb_ctx_set_timing(ctx.handle, 1 if enable else 0))
 
 
-STAGES = ("align", "zstats_tobs", "labels", "gemm_epilogue", "recheck", "finalize_copy")
+STAGES = ("align", "zstats_tobs", "labels", "gemm_epilogue", "recheck", "finalize_copy", "gemm_kernels")
 
 
 def stage_times(ctx: Context):
@@ -318,7 +318,7 @@ def stage_times(ctx: Context):
     L = lib()
     L.hb_ctx_stage_times.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
     L.hb_ctx_stage_times.restype = C.c_int
-    ms = (C.c_float * 6)()
+    ms = (C.c_float * len(STAGES))()
     nl = C.c_int32(0)
     _check(L.hb_ctx_stage_times(ctx.handle, ms, C.byref(nl)))
     return dict(zip(STAGES, [float(v) for v in ms])), int(nl.value)
