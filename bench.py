@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--B", type=int, default=9999)
     ap.add_argument("--d", type=int, default=768)
-    ap.add_argument("--path", choices=["mixed", "plain"], default="mixed")
+    ap.add_argument("--path", choices=["mixed", "mixed-2sm", "plain"], default="mixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -196,7 +196,7 @@ def main():
     from paper_2605_08048_gb300 import hbperm as H
     from paper_2605_08048_gb300 import synth
 
-    path = H.HB_PATH_MIXED if a.path == "mixed" else H.HB_PATH_FP32_PLAIN
+    path = {"mixed": H.HB_PATH_MIXED, "mixed-2sm": H.HB_PATH_MIXED_2SM, "plain": H.HB_PATH_FP32_PLAIN}[a.path]
     batch = synth.workload_batched(seed=1237 + rank, P=a.pairs) if a.d == 768 else synth.batch(1237 + rank, a.pairs,
                                                                                                a.d, "bf16")
     XYh = torch.from_numpy(batch.XY.view(np.int16)).view(torch.bfloat16)
@@ -298,7 +298,7 @@ def main():
 
     # the plain FP32 GPU path on the same workload: throughput and identical counts
     plain = None
-    if not a.no_plain and path == H.HB_PATH_MIXED:
+    if not a.no_plain and path != H.HB_PATH_FP32_PLAIN:
         po = H.make_opts(B=a.B, seed=1, path=H.HB_PATH_FP32_PLAIN)
         H.hb_perm_test_batched(ctx, XY, n, m, po)
         barrier()

@@ -77,7 +77,9 @@ typedef enum { HB_ALT_TWO_SIDED = 0, HB_ALT_GREATER = 1, HB_ALT_LESS = 2 } hb_al
 /* HB_PATH_MIXED: exact 16-bit fixed-point slices of Z on tcgen05 tensor
  * cores (BF16 operands, FP32 accumulators in TMEM), wide column tiles (128
  * z-columns per accumulator tile; 64 for FP32 input).  HB_PATH_MIXED_NARROW:
- * the same with half-width column tiles.  HB_PATH_FP32_PLAIN: the paper's
+ * the same with half-width column tiles.  HB_PATH_MIXED_2SM: wide tiles on
+ * pairs of SMs (tcgen05 cta_group::2, 256 relabellings per MMA, each SM
+ * holding half of every Z-slice tile).  HB_PATH_FP32_PLAIN: the paper's
  * Algorithm 2 taken literally (+-1 signs, FP32 SIMT GEMM).  HB_PATH_AUTO:
  * each pair takes the route the context's route table holds for its size
  * (hb_autotune; untuned: HB_PATH_MIXED up to n + m = 65536, the SIMT path
@@ -86,7 +88,8 @@ typedef enum {
     HB_PATH_MIXED = 0,
     HB_PATH_FP32_PLAIN = 1,
     HB_PATH_AUTO = 2,
-    HB_PATH_MIXED_NARROW = 3
+    HB_PATH_MIXED_NARROW = 3,
+    HB_PATH_MIXED_2SM = 4
 } hb_path;
 
 typedef struct {
@@ -182,10 +185,11 @@ void hb_plan_destroy(hb_plan *plan);
  * bucket k holds 2^(k+5) < N <= 2^(k+6).  hb_autotune times, for every
  * bucket up to min(max_N, 65536), a synthetic batch of about 2^18 rows of
  * d unit-norm values of `dtype` (pairs of size 2^(k+6), split evenly) with
- * min(opts->B, 1023) relabellings on HB_PATH_MIXED, HB_PATH_MIXED_NARROW and
- * HB_PATH_FP32_PLAIN, and stores the fastest in the context's route table,
+ * min(opts->B, 1023) relabellings on HB_PATH_MIXED, HB_PATH_MIXED_NARROW,
+ * HB_PATH_FP32_PLAIN and HB_PATH_MIXED_2SM, and stores the fastest in the
+ * context's route table,
  * which HB_PATH_AUTO then follows; buckets above 65536 always take the SIMT
- * path.  ms_out (host, nullable) receives [HB_ROUTE_BUCKETS][3] wall-clock
+ * path.  ms_out (host, nullable) receives [HB_ROUTE_BUCKETS][4] wall-clock
  * milliseconds in that path order, -1 where not timed.  The other fields of
  * opts (stat, alt, align, seed) are those of the timed runs.  Synchronous;
  * allocates and frees its own device buffer. */

@@ -260,7 +260,7 @@ static hb_status validate_opts(const hb_opts *op)
     if (op->alt < 0 || op->alt > 2) return fail(HB_ERR_INVALID_ARG, "alt %d unknown", op->alt);
     if (op->reflect_side != 0 && op->reflect_side != 1)
         return fail(HB_ERR_INVALID_ARG, "reflect_side %d unknown", op->reflect_side);
-    if (op->path < HB_PATH_MIXED || op->path > HB_PATH_MIXED_NARROW)
+    if (op->path < HB_PATH_MIXED || op->path > HB_PATH_MIXED_2SM)
         return fail(HB_ERR_INVALID_ARG, "path %d unknown", op->path);
     if (!op->exhaustive && (op->B < 1 || op->B > 0x7fffffffLL))
         return fail(HB_ERR_INVALID_ARG, "B = %lld outside [1, 2^31)", (long long)op->B);
@@ -287,14 +287,14 @@ static int32_t route_for(const hb_ctx *c, int64_t N)
 // most of the batch's rows.
 static int32_t route_for_batch(const hb_ctx *c, int64_t P, const int64_t *n, const int64_t *m)
 {
-    int64_t rows[4] = {0, 0, 0, 0};
+    int64_t rows[5] = {0, 0, 0, 0, 0};
     for (int64_t p = 0; p < P; ++p) {
         const int32_t r = route_for(c, n[p] + m[p]);
         if (r == HB_PATH_FP32_PLAIN && n[p] + m[p] > 65536) return HB_PATH_FP32_PLAIN;
         rows[r] += n[p] + m[p];
     }
     int32_t best = HB_PATH_MIXED;
-    for (int32_t r = 0; r < 4; ++r)
+    for (int32_t r = 0; r < 5; ++r)
         if (r != HB_PATH_AUTO && rows[r] > rows[best]) best = r;
     return best;
 }
@@ -314,8 +314,9 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
     o.exhaustive = op.exhaustive ? 1 : 0;
     // HB_PATH_AUTO is resolved by the caller; the narrow tensor-core route is
     // the mixed path with half-width column tiles
-    const bool narrow = op.path == HB_PATH_MIXED_NARROW;
-    o.path = align_only ? 1 : (narrow ? HB_PATH_MIXED : op.path);
+    const bool narrow = op.path == HB_PATH_MIXED_NARROW, two_sm = op.path == HB_PATH_MIXED_2SM;
+    o.path = align_only ? 1 : (narrow || two_sm ? HB_PATH_MIXED : op.path);
+    o.cg = two_sm && !align_only ? 2 : 1;
     o.d = (int)d;
     o.dtype = dtype;
     o.want_T = want_T ? 1 : 0;
@@ -872,7 +873,7 @@ extern "C" hb_status hb_perm_test(hb_ctx *c, const void *X, int64_t n, const voi
 // HB_PATH_AUTO over pairs that take different routes: one run per route on
 // the pairs of that route (XY staged on the device once if it is host memory).
 static hb_status batched_routes(hb_ctx *c, int64_t P, const void *XY, const int64_t *n, const int64_t *m, int64_t d,
-                                int32_t dtype, hb_opts op, const std::vector<int64_t> (&sel)[4], hb_result *res,
+                                int32_t dtype, hb_opts op, const std::vector<int64_t> (&sel)[5], hb_result *res,
                                 cudaStream_t s)
 {
     const size_t esz = dtype == HB_F32 ? 4 : 2;
@@ -897,7 +898,7 @@ static hb_status batched_routes(hb_ctx *c, int64_t P, const void *XY, const int6
         base = (const char *)tmp;
     }
     hb_status hs = HB_OK, first = HB_OK;
-    for (int r = 0; r < 4 && hs == HB_OK; ++r) {
+    for (int r = 0; r < 5 && hs == HB_OK; ++r) {
         const std::vector<int64_t> &ix = sel[r];
         if (ix.empty()) continue;
         const int64_t S = (int64_t)ix.size();
@@ -945,10 +946,10 @@ extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, 
     CK(cudaSetDevice(c->device));
     hb_opts op = *opts;
     if (op.path == HB_PATH_AUTO) {
-        std::vector<int64_t> sel[4];
+        std::vector<int64_t> sel[5];
         for (int64_t p = 0; p < P; ++p) sel[route_for(c, n[p] + m[p])].push_back(p);
         int used = 0, only = HB_PATH_MIXED;
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 5; ++r)
             if (!sel[r].empty()) {
                 ++used;
                 only = r;
@@ -1258,8 +1259,8 @@ extern "C" hb_status hb_autotune(hb_ctx *c, int64_t d, int32_t dtype, const hb_o
     if (hs != HB_OK) return hs;
     if (opts->exhaustive) return fail(HB_ERR_INVALID_ARG, "route tuning needs sampled relabellings");
     CK(cudaSetDevice(c->device));
-    constexpr int NR = 3;
-    const int32_t paths[NR] = {HB_PATH_MIXED, HB_PATH_MIXED_NARROW, HB_PATH_FP32_PLAIN};
+    constexpr int NR = 4;
+    const int32_t paths[NR] = {HB_PATH_MIXED, HB_PATH_MIXED_NARROW, HB_PATH_FP32_PLAIN, HB_PATH_MIXED_2SM};
     if (ms_out)
         for (int k = 0; k < HB_ROUTE_BUCKETS * NR; ++k) ms_out[k] = -1.0f;
     const int64_t rows = (int64_t)1 << 18;

@@ -71,7 +71,8 @@ struct RunOpts {
     int32_t stat, alt, align, reflect_side, exhaustive, path;
     int32_t d, d_pad, dtype, slices;
     int32_t want_T;
-    int32_t cw;      // z-columns per tensor-core column tile (128 for 2 slices, 64 for 3)
+    int32_t cw;      // z-columns per tensor-core column tile (128 for 2 slices, 64 for 3; half when narrow)
+    int32_t cg;      // tensor-core path: 1 = one CTA per MMA, 2 = CTA pairs (M = 256)
 };
 
 // ---------------------------------------------------------------------------

@@ -15,12 +15,20 @@
 // 2^24): the group sums are exact up to the residual of the slices, which the
 // error band carries as a per-column bound.
 //
-// Warp roles (320 threads, one CTA per SM, persistent over work items):
+// Warp roles (448 threads, one CTA per SM, persistent over work items):
 //   warps 0-3  epilogue: TMEM -> registers, sigma_1 = sum_s q_s D_s,
 //              sigma_2 = t - sigma_1, squared norms, band, decision
 //   warp  4    TMA producer of the B tiles
-//   warp  5    MMA issuer (one elected lane)
-//   warps 6-9  A producers (label bits -> BF16 0/1 tiles)
+//   warp  5    MMA issuer (one elected lane); with CTA pairs (CG = 2) the odd
+//              CTA's warp 5 relays its A readiness to the even CTA instead
+//   warps 6-13 A producers (label bits -> BF16 0/1 tiles): warp 6 + i
+//              expands rows 32*(i%4) .. +31, tokens 32*(i/4) .. +31 (one
+//              label word) of every stage
+// CG = 2 (HB_PATH_MIXED_2SM): the CTAs of each pair of the cluster (ranks 2k,
+// 2k+1) run tcgen05 cta_group::2 MMAs with M = 256; each holds its 128 rows of
+// A and half of the N columns of every B tile, so each SM receives half the B
+// bytes.  It is exact like the rest but not faster on GB300 at this tile
+// shape: shared-memory operand reads, not B ingress, bound both variants.
 // Every mbarrier wait is bounded (wall-clock limit); on expiry the kernel
 // raises the timeout flag, drains its own copies and MMAs, frees TMEM and
 // returns, and the host reports HB_ERR_TIMEOUT.
@@ -40,7 +48,8 @@ constexpr int MX_NS = 4;             // pipeline stages
 constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
 constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB
 constexpr int MX_STAGE_BYTES = 48 * 1024;         // A + up to 256 B-rows x 128 B
-constexpr int MX_THREADS = 320;
+constexpr int MX_APROD = 8;         // A-producer warps: two per row block, one label word each
+constexpr int MX_THREADS = 192 + 32 * MX_APROD;
 constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of 256 columns
 constexpr int MX_BAR_OFF = MX_NS * MX_STAGE_BYTES;
 constexpr int MX_CONST_OFF = MX_BAR_OFF + 256;
@@ -111,6 +120,51 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
+// try_wait with acquire at cluster scope: for barriers a peer CTA arrives on
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// bounded wait as mbar_wait, with cluster-scope acquire
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, unsigned int *timeout)
+{
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((it & 255u) == 0u) {
+            if (*(volatile unsigned int *)timeout) return false;
+            if (globaltimer() - t0 > MX_WAIT_NS) {
+                atomicExch(timeout, 1u);
+                return false;
+            }
+        }
+    }
+}
+
+// the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// arrive, with release at cluster scope, on an mbarrier of another CTA
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -126,6 +180,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// CTA pairs: a tile into this CTA's shared memory whose completion is counted
+// on an mbarrier of the pair's even CTA (bar: shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
@@ -158,18 +223,57 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// TMEM management: with CG = 2 one warp of each CTA of the pair performs the
+// allocation (same offset, same columns) collectively, and both CTAs receive
+// the same address.
+template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols)
 {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
-                 : "memory");
+    if (CG == 2)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
+                     : "memory");
+    else
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
+                     : "memory");
 }
+template <int CG>
 __device__ __forceinline__ void tmem_relinquish()
 {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (CG == 2) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    else asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
+template <int CG>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    if (CG == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T across the CTA pair (M = 256: each CTA's
+// shared memory holds its 128 rows of A and its half of the N columns of B at
+// the same offsets; each CTA's TMEM receives its 128 rows of D).  Issued by the
+// even CTA of the pair only.
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives (once the pair's prior MMAs complete) on the mbarrier at offset
+// `bar` in every CTA of ctaMask.
+__device__ __forceinline__ void umma_commit_pair_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     bar),
+                 "h"(mask)
+                 : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate
@@ -242,26 +346,43 @@ __device__ __forceinline__ uint32_t expand2(uint32_t b)
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int S, int CW>
+template <int S, int CW, int CG>
 __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
     // CW z-columns per column tile: 128 (wide) or 64 (narrow) for two slices,
-    // 64 or 32 for three
+    // 64 or 32 for three.  CG = 2: CTA pairs (ranks 2k, 2k+1) run M = 256 MMAs,
+    // each CTA holding NACC/2 rows of every B tile.
     constexpr int NACC = S * CW;  // accumulator columns of one buffer
     static_assert(NACC <= 256 && CW % 32 == 0 && NACC % 16 == 0, "column tile");
-    constexpr uint32_t B_BYTES = (uint32_t)NACC * 128u;
+    static_assert(CG == 1 || (CG == 2 && NACC % 16 == 0 && MIXED_CLUSTER % 2 == 0), "CTA pairs");
+    constexpr int BR = NACC / CG;                  // B rows of a stage in this CTA
+    constexpr uint32_t B_BYTES = (uint32_t)BR * 128u;
+    // stages: A (16 KB) + this CTA's B rows; CTA pairs hold half the B rows, so
+    // the same shared memory holds six stages instead of four
+    constexpr int STAGE = CG == 2 ? 32 * 1024 : MX_STAGE_BYTES;
+    constexpr int NS = CG == 2 ? 6 : MX_NS;
+    static_assert(NS * STAGE <= MX_BAR_OFF && MX_A_BYTES + (int)B_BYTES <= STAGE, "stage layout");
+    // CG = 2: the odd CTA reports its A stages to the even one in groups of RG
+    // (a cluster-scope release costs about as much as a stage's MMAs, so one per
+    // group rather than per stage); the even CTA waits at the first stage of each
+    // group
+    constexpr int RG = CG == 2 ? 3 : 1;
+    static_assert(NS % RG == 0 && NS >= 2 * RG, "relay groups");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = sbase + MX_BAR_OFF;
     auto full_a = [&](int s) { return bar0 + 8u * s; };
-    auto full_b = [&](int s) { return bar0 + 8u * (MX_NS + s); };
-    auto empty = [&](int s) { return bar0 + 8u * (2 * MX_NS + s); };
-    auto acc_full = [&](int b) { return bar0 + 8u * (3 * MX_NS + b); };
-    auto acc_empty = [&](int b) { return bar0 + 8u * (3 * MX_NS + 2 + b); };
-    const uint32_t drain = bar0 + 8u * (3 * MX_NS + 4);
-    uint32_t *tmem_holder = (uint32_t *)(smem + MX_BAR_OFF + 8 * (3 * MX_NS + 5));
+    auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
+    auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
+    auto acc_full = [&](int b) { return bar0 + 8u * (3 * NS + b); };
+    auto acc_empty = [&](int b) { return bar0 + 8u * (3 * NS + 2 + b); };
+    const uint32_t drain = bar0 + 8u * (3 * NS + 4);
+    // CG = 2, even CTA: the odd CTA's A tiles of stages s .. s + RG - 1 are in place
+    auto peer_ready = [&](int s) { return bar0 + 8u * (3 * NS + 5 + s); };
+    static_assert(8 * (4 * NS + 5) + 4 <= 256, "barrier block");
+    uint32_t *tmem_holder = (uint32_t *)(smem + MX_BAR_OFF + 8 * (4 * NS + 5));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RunOpts &o = P.o;
@@ -270,23 +391,26 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
     const uint32_t crank = cluster_ctarank();
     const int cid = (int)blockIdx.x / MIXED_CLUSTER, ncl = (int)gridDim.x / MIXED_CLUSTER;
     constexpr uint16_t CMASK = (uint16_t)((1u << MIXED_CLUSTER) - 1u);
+    const bool leader = CG == 1 || (crank & 1u) == 0u;  // issues the MMAs (CG = 2: the even CTA)
+    const uint16_t pair_mask = (uint16_t)((CG == 2 ? 3u : 1u) << (crank & ~(uint32_t)(CG - 1)));
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < MX_NS; ++s) {
-            mbar_init(full_a(s), 4);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full_a(s), MX_APROD);
             mbar_init(full_b(s), 1);
-            mbar_init(empty(s), MIXED_CLUSTER);  // one commit from the MMA thread of every CTA
+            mbar_init(empty(s), CG == 2 ? 1 : MIXED_CLUSTER);  // CG = 2: the pair's commit; else one per CTA
+            mbar_init(peer_ready(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
-            mbar_init(acc_empty(b), 4);
+            mbar_init(acc_empty(b), 4 * CG);  // the epilogue warps of every CTA sharing the accumulator
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        tmem_alloc(smem_u32(tmem_holder), MX_TMEM_COLS);
-        tmem_relinquish();
+        tmem_alloc<CG>(smem_u32(tmem_holder), MX_TMEM_COLS);
+        tmem_relinquish<CG>();
     }
     // every barrier of every CTA is initialised before any multicast copy or commit
     tc_fence_before();
@@ -312,38 +436,83 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                             ok = false;
                             break;
                         }
-                        // every CTA expects the tile; the cluster's first CTA fetches it once
-                        // from L2 and multicasts it into all of them (the slot is free in all
-                        // CTAs: `empty` counts one MMA commit from each)
-                        mbar_arrive_expect_tx(full_b(stage), B_BYTES);
-                        if (crank == 0)
-                            tma_load_2d_mc(sbase + stage * MX_STAGE_BYTES + MX_A_BYTES, &tmap,
-                                           (int)(pm.z_row + kc * MX_K), c * NACC, full_b(stage), CMASK);
+                        // every CTA expects its rows of the tile; the cluster's first CTA (per
+                        // half, with CTA pairs) fetches them once from L2 and multicasts them
+                        // (the slot is free in every destination: `empty` counts one commit
+                        // from every MMA-issuing CTA)
+                        if (CG == 1) {
+                            mbar_arrive_expect_tx(full_b(stage), B_BYTES);
+                            if (crank == 0)
+                                tma_load_2d_mc(sbase + stage * STAGE + MX_A_BYTES, &tmap, (int)(pm.z_row + kc * MX_K),
+                                               c * NACC, full_b(stage), CMASK);
+                        } else {
+                            // each CTA of the pair loads its half into its own shared memory and
+                            // the even CTA's barrier counts both halves
+                            if (leader) mbar_arrive_expect_tx(full_b(stage), 2u * B_BYTES);
+                            tma_load_2d_pair(sbase + stage * STAGE + MX_A_BYTES, &tmap, (int)(pm.z_row + kc * MX_K),
+                                             c * NACC + (int)(crank & 1u) * BR, mapa_rank(full_b(stage), crank & ~1u));
+                        }
                         ++issued;
-                        if (++stage == MX_NS) {
+                        if (++stage == NS) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
                 }
             }
-            // wait for this thread's copies still in flight (bounded)
-            const int inflight = (int)std::min<long long>(issued, MX_NS);
+            // wait for this thread's copies still in flight (bounded); an odd CTA's
+            // copies complete on the even CTA's barriers, which its MMA thread drains
+            const int inflight = CG == 2 && !leader ? 0 : (int)std::min<long long>(issued, NS);
             for (int k = 1; k <= inflight; ++k) {
                 int s = stage - k;
                 uint32_t ph = phase;
                 if (s < 0) {
-                    s += MX_NS;
+                    s += NS;
                     ph ^= 1u;
                 }
                 unsigned int dummy = 0;
                 mbar_wait(full_b(s), ph, ok ? P.timeout : &dummy);
             }
         }
+    } else if (warp == 5 && !leader) {
+        // ---------------- CG = 2, odd CTA: tells the even CTA when its A tiles are in ----------------
+        // (its B halves are counted on the even CTA's barriers by the copies themselves)
+        if (lane == 0) {
+            const uint32_t rank0 = crank - 1u;
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int pending = -1;  // first stage of a group not reported yet
+            for (int it = cid; it < P.n_work && ok; it += ncl) {
+                const WorkItem w = P.items[it];
+                if (P.st[w.pair].status != ST_OK) continue;
+                const PairMeta &pm = P.meta[w.pair];
+                const int KC = pm.N_pad / MX_K;
+                for (int c = 0; c < C && ok; ++c) {
+                    for (int kc = 0; kc < KC; ++kc) {
+                        if (!mbar_wait(full_a(stage), phase, P.timeout)) {
+                            ok = false;
+                            break;
+                        }
+                        if (stage % RG == 0) pending = stage;
+                        if (stage % RG == RG - 1) {
+                            mbar_arrive_remote(mapa_rank(peer_ready(pending), rank0));
+                            pending = -1;
+                        }
+                        if (++stage == NS) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            // the last group may be short: its stages are all in
+            if (ok && pending >= 0) mbar_arrive_remote(mapa_rank(peer_ready(pending), rank0));
+        }
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(MX_M, NACC);
+            constexpr uint32_t idesc = idesc_bf16(MX_M * CG, NACC);
             int stage = 0, abuf = 0;
             uint32_t phase = 0, aphase = 0;
             bool ok = true;
@@ -360,36 +529,49 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)abuf * 256u;
                     for (int kc = 0; kc < KC; ++kc) {
-                        if (!mbar_wait(full_a(stage), phase, P.timeout) || !mbar_wait(full_b(stage), phase, P.timeout)) {
+                        if (!mbar_wait(full_a(stage), phase, P.timeout) || !mbar_wait(full_b(stage), phase, P.timeout) ||
+                            (CG == 2 && stage % RG == 0 && !mbar_wait_cluster(peer_ready(stage), phase, P.timeout))) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a0 = sbase + stage * MX_STAGE_BYTES, b0 = a0 + MX_A_BYTES;
+                        const uint32_t a0 = sbase + stage * STAGE, b0 = a0 + MX_A_BYTES;
+                        if (CG == 2) {
 #pragma unroll
-                        for (int k = 0; k < MX_K / 16; ++k)
-                            umma_bf16(dt, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
-                                      (kc | k) != 0 ? 1u : 0u);
-                        umma_commit_mc(empty(stage), CMASK);  // frees this slot in every CTA's view
-                        if (++stage == MX_NS) {
+                            for (int k = 0; k < MX_K / 16; ++k)
+                                umma_bf16_pair(dt, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
+                                               (kc | k) != 0 ? 1u : 0u);
+                            umma_commit_pair_mc(empty(stage), pair_mask);  // frees this slot in both CTAs
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < MX_K / 16; ++k)
+                                umma_bf16(dt, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
+                                          (kc | k) != 0 ? 1u : 0u);
+                            umma_commit_mc(empty(stage), CMASK);  // frees this slot in every CTA's view
+                        }
+                        if (++stage == NS) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
                     if (!ok) break;
-                    umma_commit(acc_full(abuf));
+                    if (CG == 2) umma_commit_pair_mc(acc_full(abuf), pair_mask);  // both CTAs' epilogues
+                    else umma_commit(acc_full(abuf));
                     abuf ^= 1;
                     if (abuf == 0) aphase ^= 1u;
                 }
             }
             // all MMAs issued by this thread have completed once `drain` flips
-            umma_commit(drain);
+            if (CG == 2) umma_commit_pair_mc(drain, (uint16_t)(1u << crank));
+            else umma_commit(drain);
             unsigned int dummy = 0;
             mbar_wait(drain, 0, ok ? P.timeout : &dummy);
         }
     } else if (warp >= 6) {
         // ---------------- A producers: label bits -> BF16 0/1 ----------------
-        const int r = threadIdx.x - 6 * 32;  // relabelling row of the tile, 0..127
+        const int pi = warp - 6;
+        const int r = (pi & 3) * 32 + lane;  // relabelling row of the tile, 0..127
+        const int half = pi >> 2;            // tokens 32*half .. 32*half+31 of each stage
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -400,19 +582,18 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
             const int KC = pm.N_pad / MX_K;
             const int tile = w.tile * MIXED_CLUSTER + (int)crank;
             const uint32_t *lab = P.bits + pm.lab_off + (int64_t)tile * MX_M + r;
-            // label words of K-chunk kc (identical for every column tile)
-            auto words = [&](int kc, uint32_t &lo, uint32_t &hi) {
-                const int w0 = 2 * kc;
-                lo = w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
-                hi = w0 + 1 < pm.W ? __ldg(lab + (int64_t)(w0 + 1) * pm.B_pad) : 0u;
+            // this warp's label word of K-chunk kc (identical for every column tile)
+            auto word = [&](int kc) {
+                const int w0 = 2 * kc + half;
+                return w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
             };
             // loads run MX_PF stages ahead of the expansion (a register ring,
             // wrapping across column tiles), which covers the DRAM latency
-            uint32_t rlo[MX_PF], rhi[MX_PF];
+            uint32_t rw[MX_PF];
             int knext = 0;  // K-chunk of the next load
 #pragma unroll
             for (int i = 0; i < MX_PF; ++i) {
-                words(knext, rlo[i], rhi[i]);
+                rw[i] = word(knext);
                 if (++knext == KC) knext = 0;
             }
             for (int c = 0; c < C && ok; ++c) {
@@ -422,18 +603,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                         ok = false;
                         break;
                     }
-                    const uint32_t lo = rlo[0], hi = rhi[0];
+                    const uint32_t wd = rw[0];
 #pragma unroll
-                    for (int i = 0; i + 1 < MX_PF; ++i) {
-                        rlo[i] = rlo[i + 1];
-                        rhi[i] = rhi[i + 1];
-                    }
-                    words(knext, rlo[MX_PF - 1], rhi[MX_PF - 1]);
+                    for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
+                    rw[MX_PF - 1] = word(knext);
                     if (++knext == KC) knext = 0;
-                    uint8_t *row = smem + stage * MX_STAGE_BYTES + r * 128;
+                    uint8_t *row = smem + stage * STAGE + r * 128;
 #pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
-                        const uint32_t b8 = ((ch < 4 ? lo : hi) >> ((ch & 3) * 8)) & 0xffu;
+                    for (int cl = 0; cl < 4; ++cl) {
+                        const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
+                        const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
                         uint4 v;
                         v.x = expand2(b8);
                         v.y = expand2(b8 >> 2);
@@ -444,7 +623,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full_a(stage));
-                    if (++stage == MX_NS) {
+                    if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -512,7 +691,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty(abuf));
+                if (lane == 0) {
+                    if (leader) mbar_arrive(acc_empty(abuf));
+                    else mbar_arrive_remote(mapa_rank(acc_empty(abuf), crank - 1u));  // the even CTA reuses it
+                }
                 abuf ^= 1;
                 if (abuf == 0) aphase ^= 1u;
                 Q1 += (double)tq1;
@@ -552,7 +734,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
     cluster_sync();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, MX_TMEM_COLS);
+        tmem_dealloc<CG>(tmem, MX_TMEM_COLS);
     }
 }
 
@@ -584,7 +766,8 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     }
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode(err);
     if (!enc) return cudaErrorNotSupported;
-    const int nacc = S * a.o.cw;
+    const int CGv = a.o.cg == 2 ? 2 : 1;
+    const int nacc = S * a.o.cw / CGv;  // B rows of one CTA's share of a tile
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)a.zq_ld, (cuuint64_t)a.zq_rows};
     const cuuint64_t gstride[1] = {(cuuint64_t)a.zq_ld * 2};
@@ -612,8 +795,9 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     prm.timeout = a.timeout;
     prm.T_out = a.T_out;
     void (*kern)(const CUtensorMap, const MixedParams) = nullptr;
-    if (S == 2) kern = a.o.cw == 128 ? k_mixed<2, 128> : a.o.cw == 64 ? k_mixed<2, 64> : nullptr;
-    else kern = a.o.cw == 64 ? k_mixed<3, 64> : a.o.cw == 32 ? k_mixed<3, 32> : nullptr;
+    if (CGv == 2) kern = S == 2 && a.o.cw == 128 ? k_mixed<2, 128, 2> : S == 3 && a.o.cw == 64 ? k_mixed<3, 64, 2> : nullptr;
+    else if (S == 2) kern = a.o.cw == 128 ? k_mixed<2, 128, 1> : a.o.cw == 64 ? k_mixed<2, 64, 1> : nullptr;
+    else kern = a.o.cw == 64 ? k_mixed<3, 64, 1> : a.o.cw == 32 ? k_mixed<3, 32, 1> : nullptr;
     if (!kern) {
         err = "unsupported column tile width";
         return cudaErrorInvalidValue;

@@ -18,7 +18,8 @@ HB_OK, HB_ERR_INVALID_ARG, HB_ERR_DEGENERATE, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TI
 HB_F32, HB_BF16 = 0, 1
 HB_STAT_LOGVOL_VMF, HB_STAT_ONE_MINUS_R2, HB_STAT_MEAN_COSDIST = 0, 1, 2
 HB_ALT_TWO_SIDED, HB_ALT_GREATER, HB_ALT_LESS = 0, 1, 2
-HB_PATH_MIXED, HB_PATH_FP32_PLAIN, HB_PATH_AUTO, HB_PATH_MIXED_NARROW = 0, 1, 2, 3
+HB_PATH_MIXED, HB_PATH_FP32_PLAIN, HB_PATH_AUTO, HB_PATH_MIXED_NARROW, HB_PATH_MIXED_2SM = 0, 1, 2, 3, 4
+ROUTE_PATHS = (HB_PATH_MIXED, HB_PATH_MIXED_NARROW, HB_PATH_FP32_PLAIN, HB_PATH_MIXED_2SM)  # hb_autotune's order
 ROUTE_BUCKETS = 15  # size buckets of the route table (hb_autotune)
 
 
@@ -269,15 +270,15 @@ class Plan:
 
 
 def autotune(ctx: Context, d: int, dtype, opts: hb_opts, max_N: int = 65536):
-    """Times the three routes per size bucket and fills the context's route
-    table; returns the [ROUTE_BUCKETS][3] wall-clock ms (MIXED, MIXED_NARROW,
-    FP32_PLAIN; -1 = not timed) as a numpy array."""
+    """Times the routes per size bucket and fills the context's route table;
+    returns the [ROUTE_BUCKETS][len(ROUTE_PATHS)] wall-clock ms (in
+    ROUTE_PATHS order; -1 = not timed) as a numpy array."""
     import numpy as np
 
     code = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
-    ms = (C.c_float * (ROUTE_BUCKETS * 3))()
+    ms = (C.c_float * (ROUTE_BUCKETS * len(ROUTE_PATHS)))()
     _check(lib().hb_autotune(ctx.handle, int(d), code, C.byref(opts), int(max_N), ms))
-    return np.array(ms[:], dtype=np.float32).reshape(ROUTE_BUCKETS, 3)
+    return np.array(ms[:], dtype=np.float32).reshape(ROUTE_BUCKETS, len(ROUTE_PATHS))
 
 
 def route(ctx: Context, N: int) -> int:

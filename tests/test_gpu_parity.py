@@ -15,7 +15,8 @@ from paper_2605_08048_gb300 import synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 PATHS = [pytest.param(H.HB_PATH_FP32_PLAIN, id="plain"), pytest.param(H.HB_PATH_MIXED, id="mixed"),
-         pytest.param(H.HB_PATH_MIXED_NARROW, id="mixed-narrow")]
+         pytest.param(H.HB_PATH_MIXED_NARROW, id="mixed-narrow"), pytest.param(H.HB_PATH_MIXED_2SM, id="mixed-2sm")]
+TENSOR_PATHS = (H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW, H.HB_PATH_MIXED_2SM)
 
 
 def dev(a: np.ndarray):
@@ -105,8 +106,8 @@ def test_plain_workload_parity(ctx, path):
     _compare(res, T, ref, Tref, O.STAT_LOGVOL_VMF)
     # the fast path itself decides almost every relabelling: its group sums are
     # accurate, not rescued by the exact recheck
-    assert res["n_rechecked"] <= (0.01 if path in (H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW) else 0.10) * 999
-    assert 0.0 < res["band_max"] < (1e-4 if path in (H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW) else 2e-2)
+    assert res["n_rechecked"] <= (0.01 if path in TENSOR_PATHS else 0.10) * 999
+    assert 0.0 < res["band_max"] < (1e-4 if path in TENSOR_PATHS else 2e-2)
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -120,7 +121,7 @@ def test_fast_path_statistics_match_oracle(ctx, path):
     _compare(res, T, ref, Tref, O.STAT_LOGVOL_VMF)
     err = np.abs(T.cpu().numpy().astype(np.float64) - Tref)
     assert err.max() <= res["band_max"] + 1e-6
-    assert res["n_rechecked"] <= (0.01 if path in (H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW) else 0.10) * 2000
+    assert res["n_rechecked"] <= (0.01 if path in TENSOR_PATHS else 0.10) * 2000
 
 
 @pytest.mark.parametrize("path", PATHS)

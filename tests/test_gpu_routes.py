@@ -73,11 +73,11 @@ def test_auto_sends_large_pairs_to_simt(ctx):
 def test_autotune_fills_the_route_table(ctx):
     opts = H.make_opts(B=255, seed=1)
     ms = H.autotune(ctx, 128, torch.bfloat16, opts, max_N=1024)
-    assert ms.shape == (H.ROUTE_BUCKETS, 3)
+    assert ms.shape == (H.ROUTE_BUCKETS, len(H.ROUTE_PATHS))
     assert (ms[:5] > 0).all() and (ms[5:] == -1).all()  # buckets up to N = 1024 timed
     for k in range(5):
         N = 64 << k
-        assert H.route(ctx, N) == [H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW, H.HB_PATH_FP32_PLAIN][int(np.argmin(ms[k]))]
+        assert H.route(ctx, N) == H.ROUTE_PATHS[int(np.argmin(ms[k]))]
     assert H.route(ctx, 70000) == H.HB_PATH_FP32_PLAIN
     b = synth.batch(102, 6, d=128, dtype="bf16", sizes=([20, 60, 200, 400, 33, 700], [30, 64, 180, 500, 31, 300]))
     XY = dev(b.XY)
