@@ -58,6 +58,12 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--triage", action="store_true",
+                    help="learned triage at scale: train on --train-pairs of the method's own runs, triage "
+                         "--eval-pairs held-out pairs in chunks of 4096 (one JSON line)")
+    ap.add_argument("--train-pairs", type=int, default=200_000)
+    ap.add_argument("--eval-pairs", type=int, default=50_000)
+    ap.add_argument("--epochs", type=int, default=30)
     return ap.parse_args()
 
 
@@ -174,10 +180,42 @@ def run_reference(a):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def run_triage(a):
+    """The learned triage at scale: time and decision error against testing
+    every pair (B = 9999, alpha = 0.05, band [0.005, 0.2], 2 % audit)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2605_08048_gb300 import build as _build
+
+    _build.build()
+    from paper_2605_08048_gb300 import hbperm as H
+    from paper_2605_08048_gb300 import triage as TR
+
+    ctx = H.Context(0)
+    rep = TR.evaluate_at_scale(ctx, a.train_pairs, a.eval_pairs, epochs=a.epochs,
+                               log=lambda msg: print(msg, file=sys.stderr, flush=True))
+    t_tri = rep["seconds_features"] + rep["seconds_full_subset"]
+    line = {"impl": "triage", "metric": "pair decisions/s with learned triage (B=9999, alpha=0.05)",
+            "value": rep["pairs"] / t_tri, "unit": "pair decisions/s", "higher_is_better": True,
+            "baseline_every_pair_tested": rep["pairs"] / rep["seconds_full_all"], "data": "synthetic",
+            "config": {"workload": "triage: held-out pairs of the batched recipe (d=768 BF16, half null), chunks of 4096",
+                       "train_pairs": rep["train_pairs"], "eval_pairs": rep["pairs"], "epochs": rep["epochs"]},
+            **{k: rep[k] for k in ("skipped_fraction", "decision_error_skipped", "audit_decision_error", "audited",
+                                   "skipped", "full_tested", "speedup", "loss_first", "loss_last",
+                                   "seconds_training_data", "seconds_training", "seconds_features",
+                                   "seconds_full_subset", "seconds_full_all")}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.triage:
+        return run_triage(a)
 
     import torch
 

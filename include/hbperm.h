@@ -239,7 +239,7 @@ hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, int64_t m, i
 
 /* Features of P pairs (packed as for hb_perm_test_batched; XY device):
  * log n, log m, log(d * lambda_k) for the 16 Ritz values lambda_k of the
- * pooled scatter Z^T Z / N of the aligned pair (Sec. 3.1) after 4 block
+ * pooled scatter Z^T Z / N of the aligned pair (Sec. 3.1) after 2 block
  * subspace iterations V <- orth(Z^T Z V / N) from a fixed Philox start block
  * (any orthonormal basis of the iterate's span gives the same Ritz values),
  * and 10 * T_obs.  Runs the alignment and T_obs only (no relabellings).

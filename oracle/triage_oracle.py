@@ -22,7 +22,7 @@ import numpy as np
 from . import oracle as O
 
 K_RITZ = 16
-RITZ_ITERS = 4
+RITZ_ITERS = 2
 LEVELS = np.array([0.5, 0.8, 0.9, 0.95, 0.975, 0.99, 0.995, 0.998, 0.999])
 N_FEAT = 19
 HIDDEN = 256

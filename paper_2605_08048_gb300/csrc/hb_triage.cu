@@ -17,7 +17,7 @@
 namespace hb {
 
 constexpr int RK = 16;          // Ritz block size
-constexpr int RITZ_ITERS = 4;
+constexpr int RITZ_ITERS = 2;
 constexpr int MLP_IN = 19, MLP_H = 256, MLP_OUT = 9;
 
 // ---------------------------------------------------------------------------

@@ -123,6 +123,36 @@ def batch(seed: int, P: int, d: int = 768, dtype: str = "bf16", sizes=None, sigm
     return Batch(XY, n, m, d, dtype, null)
 
 
+def batch_device(seed: int, P: int, d: int = 768, sigma: float = 0.35, alt_ratio: float = 1.1, device="cuda",
+                 null_fraction: float = 0.5) -> Batch:
+    """The batched recipe generated on the GPU (for batches too large to draw
+    on the host): the same lognormal sizes and cloud model as `batch`, rows =
+    normalize(mu + sigma N(0, I)) rounded to BF16, with torch's device
+    generator seeded by `seed` (a different random stream from `batch`'s).
+    The first null_fraction of the pairs are null, the rest alternatives
+    (sigma_X = alt_ratio * sigma).  XY is a BF16 CUDA tensor."""
+    import torch
+
+    n, m = lognormal_sizes(seed, P)
+    n = np.asarray(n, dtype=np.int64)
+    m = np.asarray(m, dtype=np.int64)
+    null = np.arange(P) < int(round(null_fraction * P))
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    mu = torch.randn((2 * P, d), generator=g, device=device)
+    mu /= mu.norm(dim=1, keepdim=True)                     # pair p: rows 2p (X), 2p+1 (Y)
+    sig = torch.tensor(np.stack([np.where(null, sigma, sigma * alt_ratio), np.full(P, sigma)], 1).reshape(-1),
+                       dtype=torch.float32, device=device)
+    sizes = torch.from_numpy(np.stack([n, m], 1).reshape(-1)).to(device)
+    owner = torch.repeat_interleave(torch.arange(2 * P, device=device), sizes)
+    XY = torch.empty((int(sizes.sum()), d), dtype=torch.bfloat16, device=device)
+    step = 1 << 18
+    for r0 in range(0, XY.shape[0], step):                 # bounded FP32 scratch
+        o = owner[r0:r0 + step]
+        x = torch.randn((o.numel(), d), generator=g, device=device) * sig[o, None] + mu[o]
+        XY[r0:r0 + step] = (x / x.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+    return Batch(XY, n, m, d, "bf16", null)
+
+
 # Workload recipes (sizes and distributions of the paper's workloads).
 def workload_plain(seed: int = 1235):
     """Single test: n=200, m=300, d=768, FP32, sigma 0.35 both, independent

@@ -36,15 +36,24 @@ def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
     return torch.from_numpy(flat).to(device)
 
 
-def _dev_bf16(xy_bits: np.ndarray) -> torch.Tensor:
-    return torch.from_numpy(np.ascontiguousarray(xy_bits).view(np.int16)).view(torch.bfloat16).cuda()
+def _dev_bf16(xy) -> torch.Tensor:
+    """The batch's rows on the device (BF16 bit patterns from numpy, or a tensor as is)."""
+    if isinstance(xy, torch.Tensor):
+        return xy if xy.is_cuda else xy.cuda()
+    return torch.from_numpy(np.ascontiguousarray(xy).view(np.int16)).view(torch.bfloat16).cuda()
+
+
+def _on_device(b) -> torch.Tensor:
+    if isinstance(b.XY, torch.Tensor) or b.XY.dtype == np.uint16:
+        return _dev_bf16(b.XY)
+    return torch.from_numpy(b.XY).cuda()
 
 
 def training_set(ctx: H.Context, batches, opts: H.hb_opts):
     """Features and null-quantile targets of the pairs of each synthetic batch."""
     feats, targets = [], []
     for b in batches:
-        XY = _dev_bf16(b.XY) if b.XY.dtype == np.uint16 else torch.from_numpy(b.XY).cuda()
+        XY = _on_device(b)
         f, _, r1 = H.triage_features(ctx, XY, b.n, b.m, opts)
         q, r2 = H.null_quantiles(ctx, XY, b.n, b.m, opts)
         ok = torch.tensor([a["status"] == 0 and c["status"] == 0 for a, c in zip(r1, r2)], device=f.device)
@@ -92,7 +101,7 @@ def triage(ctx: H.Context, net: H.MLP, batch, opts: H.hb_opts, alpha: float = 0.
            audit: float = 0.02, seed: int = 0, evaluate_all: bool = True) -> TriageReport:
     """Routes the pairs of `batch`: full test for predicted p in `band` and for
     an audit sample; the others are decided by the predicted p."""
-    XY = _dev_bf16(batch.XY) if batch.XY.dtype == np.uint16 else torch.from_numpy(batch.XY).cuda()
+    XY = _on_device(batch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     feat, tobs, res = H.triage_features(ctx, XY, batch.n, batch.m, opts)
@@ -109,11 +118,10 @@ def triage(ctx: H.Context, net: H.MLP, batch, opts: H.hb_opts, alpha: float = 0.
     t_sub = 0.0
     p_full = np.full(P, np.nan)
     if len(sub):
-        b2 = _subset(batch, sub)
-        X2 = _dev_bf16(b2.XY) if b2.XY.dtype == np.uint16 else torch.from_numpy(b2.XY).cuda()
+        X2, n2, m2 = pack(XY, batch.n, batch.m, sub)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = H.hb_perm_test_batched(ctx, X2, b2.n, b2.m, opts)
+        r = H.hb_perm_test_batched(ctx, X2, n2, m2, opts)
         t_sub = time.perf_counter() - t0
         p_full[sub] = [x["p"] for x in r]
     t_all = float("nan")
@@ -133,9 +141,60 @@ def triage(ctx: H.Context, net: H.MLP, batch, opts: H.hb_opts, alpha: float = 0.
                         t_feat, t_sub, t_all, p_hat, p_all if evaluate_all else p_full)
 
 
-def _subset(batch, idx):
-    from .synth import Batch
+def pack(XY: torch.Tensor, n, m, idx):
+    """The pairs `idx` of a packed device batch as a new packed batch."""
+    from .shard import pack as _pack
 
-    off = batch.offsets
-    rows = np.concatenate([np.arange(off[p], off[p + 1]) for p in idx])
-    return Batch(batch.XY[rows], batch.n[idx], batch.m[idx], batch.d, batch.dtype, batch.null[idx])
+    return _pack(XY, n, m, np.asarray(idx))
+
+
+def evaluate_at_scale(ctx: H.Context, train_pairs: int = 200_000, eval_pairs: int = 50_000, chunk: int = 4096,
+                      opts: H.hb_opts = None, epochs: int = 30, lr: float = 2e-3, alpha: float = 0.05,
+                      band=(0.005, 0.2), audit: float = 0.02, seed: int = 0, log=None) -> dict:
+    """Trains the network on the method's own runs of `train_pairs` synthetic
+    pairs of the batched recipe, then triages `eval_pairs` held-out pairs in
+    chunks of `chunk`, testing every pair fully as well to measure the
+    decision error and the time the triage saves.  Returns the totals."""
+    from . import synth
+
+    opts = opts or H.make_opts(B=9999, seed=1)
+    say = log or (lambda *_: None)
+    t0 = time.perf_counter()
+    feats, targets = [], []
+    for k, c0 in enumerate(range(0, train_pairs, chunk)):
+        b = synth.batch_device(100_000 + k, min(chunk, train_pairs - c0))
+        f, q = training_set(ctx, [b], opts)
+        feats.append(f)
+        targets.append(q)
+        del b
+    feat, target = torch.cat(feats), torch.cat(targets)
+    t_data = time.perf_counter() - t0
+    say(f"training set: {feat.shape[0]} pairs in {t_data:.1f} s")
+    t0 = time.perf_counter()
+    net, hist = train(ctx, feat, target, epochs=epochs, batch=1024, lr=lr, seed=seed)
+    t_train = time.perf_counter() - t0
+    say(f"training: loss {hist[0]:.4f} -> {hist[-1]:.4f} in {t_train:.1f} s")
+    warm = synth.batch_device(199_999, 256)
+    triage(ctx, net, warm, opts, alpha, band, audit, seed=seed)  # workspace sizing
+    tot = dict(pairs=0, skipped=0, full_tested=0, audited=0, audit_wrong=0, skipped_wrong=0, seconds_features=0.0,
+               seconds_full_subset=0.0, seconds_full_all=0.0)
+    for k, c0 in enumerate(range(0, eval_pairs, chunk)):
+        b = synth.batch_device(200_000 + k, min(chunk, eval_pairs - c0))
+        r = triage(ctx, net, b, opts, alpha, band, audit, seed=seed + k)
+        tot["pairs"] += r.pairs
+        tot["skipped"] += r.skipped
+        tot["full_tested"] += r.full_tested
+        tot["audited"] += r.audited
+        tot["audit_wrong"] += int(round(r.audit_decision_error * r.audited)) if r.audited else 0
+        tot["skipped_wrong"] += int(round(r.decision_error_skipped * r.skipped)) if r.skipped else 0
+        tot["seconds_features"] += r.seconds_features
+        tot["seconds_full_subset"] += r.seconds_full_subset
+        tot["seconds_full_all"] += r.seconds_full_all
+        del b
+    tot.update(train_pairs=int(feat.shape[0]), epochs=epochs, loss_first=hist[0], loss_last=hist[-1],
+               seconds_training_data=t_data, seconds_training=t_train,
+               decision_error_skipped=tot["skipped_wrong"] / max(1, tot["skipped"]),
+               audit_decision_error=tot["audit_wrong"] / max(1, tot["audited"]),
+               skipped_fraction=tot["skipped"] / max(1, tot["pairs"]),
+               speedup=tot["seconds_full_all"] / max(1e-9, tot["seconds_features"] + tot["seconds_full_subset"]))
+    return tot
