@@ -218,13 +218,21 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
         __syncthreads();
     }
     // element pass: z = fl_storage(fma(-2c, u_j, x)) or a copy
+    constexpr int RB = 8;  // rows whose loads are issued together
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const double uj = reflect ? up[j] : 0.0;
         float mx = 0.0f;
-        for (int r = 0; r < ch.nrows; ++r) {
-            const int64_t si = (int64_t)(ch.row0 + r) * d + j;
+        for (int rb = 0; rb < ch.nrows; rb += RB) {
+        uint32_t xv[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            xv[k] = rb + k < ch.nrows ? load_f32bits(src, DT, (int64_t)(ch.row0 + rb + k) * d + j) : 0u;
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const int r = rb + k;
+            if (r >= ch.nrows) break;
             const int64_t zi = (zrow0 + r) * d + j;
-            const uint32_t xb = load_f32bits(src, DT, si);
+            const uint32_t xb = xv[k];
             float zf;
             if (reflect) {
                 const double zv = __fma_rn(cs[r], uj, (double)__uint_as_float(xb));
@@ -236,6 +244,7 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
                 zf = __uint_as_float(xb);
             }
             mx = fmaxf(mx, fabsf(zf));
+        }
         }
         if (colmax) atomicMax(colmax + (int64_t)ch.pair * o.d_pad + j, __float_as_uint(mx));
     }
@@ -332,9 +341,16 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
         WinAcc wa;
         wa.init(col_bound_exp(mb));
         float cacc = 0.0f;
-        const int r1 = min(ch.nrows, (part + 1) * ZS_ROWS);
-        for (int r = part * ZS_ROWS; r < r1; ++r) {
-            const uint32_t b = j < d ? load_f32bits(Z, DT, (zrow0 + r) * d + j) : 0u;
+        const int r0 = part * ZS_ROWS, nr = max(0, min(ch.nrows - r0, ZS_ROWS));
+        // this thread's values first (all loads in flight), then the arithmetic
+        uint32_t bv[ZS_ROWS];
+#pragma unroll
+        for (int k = 0; k < ZS_ROWS; ++k) bv[k] = (k < nr && j < d) ? load_f32bits(Z, DT, (zrow0 + r0 + k) * d + j) : 0u;
+#pragma unroll
+        for (int k = 0; k < ZS_ROWS; ++k) {
+            if (k >= nr) break;
+            const int r = r0 + k;
+            const uint32_t b = bv[k];
             wa.add(b);
             const float z = __uint_as_float(b);
             if (mixed) {
