@@ -128,3 +128,17 @@ def test_triage_gains_over_testing_every_pair(ctx):
     assert rep.skipped >= 0.4 * rep.pairs
     assert rep.decision_error_skipped <= 0.05
     assert rep.seconds_features + rep.seconds_full_subset < rep.seconds_full_all
+
+
+def test_evaluate_at_scale_small(ctx):
+    """The at-scale evaluation path (device-drawn pairs, chunks) on a small
+    case: every held-out pair is either fully tested or skipped, and the
+    reported rates are consistent.  (A network trained on 3000 pairs is not
+    accurate; the accuracy is measured by the test above and, at 200k / 50k
+    pairs, by the benchmark's triage mode.)"""
+    rep = TR.evaluate_at_scale(ctx, train_pairs=3000, eval_pairs=2500, chunk=1024, epochs=30)
+    assert rep["pairs"] == 2500 and rep["train_pairs"] == 3000
+    assert rep["skipped"] + rep["full_tested"] == 2500
+    assert 0.0 <= rep["decision_error_skipped"] <= 0.5 and 0.0 <= rep["audit_decision_error"] <= 1.0
+    assert rep["loss_last"] < rep["loss_first"]
+    assert rep["seconds_full_all"] > 0 and rep["speedup"] > 0

@@ -80,3 +80,4 @@ def test_two_gloo_ranks_equal_one_process(tmp_path):
         assert list(got[0].astype(np.int64)) == [r["count"] for r in ref]
         assert list(got[1]) == [r["p"] for r in ref]
         assert np.all(got[2] == 1.5)  # the slowest rank's time on every rank
+
