@@ -177,7 +177,7 @@ __device__ __forceinline__ void store_z(void *Z, int64_t idx, double v)
 }
 
 template <int DT>
-__global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
+__global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
                                                  const RunOpts o, const PairState *__restrict__ st,
                                                  const double *__restrict__ u, void *__restrict__ Z,
                                                  unsigned int *__restrict__ colmax)
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
     __shared__ float xs[CHUNK_ROWS][RT + 1];
     __shared__ double us[RT];
     __shared__ double cs[CHUNK_ROWS];
+    __shared__ float cs32[CHUNK_ROWS];
     const RowChunk ch = chunks[blockIdx.x];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
@@ -199,28 +200,40 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
         double c = 0.0;
         for (int j0 = 0; j0 < d; j0 += RT) {
             const int w = min(RT, d - j0);
-            for (int t = threadIdx.x; t < CHUNK_ROWS * RT; t += blockDim.x) {
-                const int r = t / RT, jj = t % RT;
-                float v = 0.0f;
-                if (r < ch.nrows && jj < w)
-                    v = __uint_as_float(load_f32bits(src, DT, (int64_t)(ch.row0 + r) * d + j0 + jj));
-                xs[r][jj] = v;
+            // loads in batches of eight in flight before their stores (blockDim.x == 128)
+            constexpr int PER = CHUNK_ROWS * RT / 128, LB = 8;
+#pragma unroll 1
+            for (int k0 = 0; k0 < PER; k0 += LB) {
+                uint32_t xv[LB];
+#pragma unroll
+                for (int k = 0; k < LB; ++k) {
+                    const int t = threadIdx.x + 128 * (k0 + k), r = t / RT, jj = t % RT;
+                    xv[k] = (r < ch.nrows && jj < w) ? load_f32bits(src, DT, (int64_t)(ch.row0 + r) * d + j0 + jj)
+                                                      : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < LB; ++k) {
+                    const int t = threadIdx.x + 128 * (k0 + k);
+                    xs[t / RT][t % RT] = __uint_as_float(xv[k]);
+                }
             }
             if (threadIdx.x < RT) us[threadIdx.x] = threadIdx.x < w ? up[j0 + threadIdx.x] : 0.0;
             __syncthreads();
             if (threadIdx.x < ch.nrows) {
                 const int r = threadIdx.x;
-                for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], (double)xs[r][jj], c);
+                for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], f32_to_f64(xs[r][jj]), c);
             }
             __syncthreads();
         }
         cs[threadIdx.x] = -2.0 * c;  // exact scaling by -2
+        cs32[threadIdx.x] = __double2float_rn(-2.0 * c);
         __syncthreads();
     }
     // element pass: z = fl_storage(fma(-2c, u_j, x)) or a copy
     constexpr int RB = 8;  // rows whose loads are issued together
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const double uj = reflect ? up[j] : 0.0;
+        const float uj32 = __double2float_rn(uj);
         float mx = 0.0f;
         for (int rb = 0; rb < ch.nrows; rb += RB) {
         uint32_t xv[RB];
@@ -234,7 +247,24 @@ __global__ void __launch_bounds__(128) k_reflect(const PairMeta *__restrict__ me
             const int64_t zi = (zrow0 + r) * d + j;
             const uint32_t xb = xv[k];
             float zf;
-            if (reflect) {
+            if (reflect && DT == DT_BF16) {
+                // FP32 enclosure [y - E, y + E] of v = fl64(a u_j + x), a = -2c:
+                // a and u_j rounded to FP32 give |a u_j - a32 u32| <= 2^-23 |a32 u32| (1 + 2^-23),
+                // the FP32 fma adds <= 2^-24 |y|, the FP64 fma <= 2^-53 |v|; E is at least
+                // twice that, so it also covers the roundings of y -/+ E and of E itself.
+                // BF16 rounding is monotone: equal roundings of both ends are the rounding
+                // of v.  Otherwise (or for tiny y) the FP64 expression decides.
+                const float x = __uint_as_float(xb);
+                const float a32 = cs32[r];
+                const float y = __fmaf_rn(a32, uj32, x);
+                const float E = __fmaf_rn(__fadd_rn(fabsf(__fmul_rn(a32, uj32)), fabsf(y)), 0x1p-21f, 0x1p-126f);
+                const unsigned short zl = f32_to_bf16_rn_bits(__fsub_rn(y, E));
+                unsigned short zb = zl;
+                if (zl != f32_to_bf16_rn_bits(__fadd_rn(y, E)) || !(fabsf(y) >= 0x1p-100f))
+                    zb = f64_to_bf16_rn(__fma_rn(cs[r], uj, f32_to_f64(x)));
+                reinterpret_cast<unsigned short *>(Z)[zi] = zb;
+                zf = __uint_as_float((uint32_t)zb << 16);
+            } else if (reflect) {
                 const double zv = __fma_rn(cs[r], uj, (double)__uint_as_float(xb));
                 store_z<DT>(Z, zi, zv);
                 zf = (DT == DT_F32) ? __double2float_rn(zv) : __uint_as_float((uint32_t)f64_to_bf16_rn(zv) << 16);

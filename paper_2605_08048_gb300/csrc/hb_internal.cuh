@@ -244,6 +244,26 @@ __device__ __forceinline__ uint16_t f64_to_bf16_rn(double x)
     return (uint16_t)(sign | (uint16_t)k);  // k == 128 encodes the smallest normal
 }
 
+// BF16 bits of a normal or subnormal FP32 value, round to nearest even (the
+// same result as f64_to_bf16_rn of the exactly widened value).
+__device__ __forceinline__ unsigned short f32_to_bf16_rn_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (unsigned short)((b + 0x7fffu + ((b >> 16) & 1u)) >> 16);
+}
+
+// Exact FP32 -> FP64 widening built from the bit fields (normal values);
+// zero, subnormals, infinities and NaN take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint64_t db = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                        ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)db);
+}
+
 // ---------------------------------------------------------------------------
 // Exact-path statistic (FP64, correctly rounded operations only).
 // ---------------------------------------------------------------------------

@@ -6,9 +6,11 @@ run when the compiled library is missing -- there is no CPU fallback.
 """
 from __future__ import annotations
 
+import collections.abc
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,6 +61,59 @@ class hb_result(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# hb_result as a numpy structured type with the same field offsets
+_RESULT_KEYS = [k for k, _ in hb_result._fields_]
+RESULT_DTYPE = np.dtype({
+    "names": _RESULT_KEYS,
+    "formats": [np.float64 if t is C.c_double else (np.int64 if t is C.c_int64 else np.int32)
+                for _, t in hb_result._fields_],
+    "offsets": [getattr(hb_result, k).offset for k in _RESULT_KEYS],
+    "itemsize": C.sizeof(hb_result),
+})
+
+
+class Results(collections.abc.Sequence):
+    """Per-pair results of a batched call in one structured numpy array
+    (`array`, fields as hb_result); element i is the same dict that
+    hb_result.as_dict gives, built when it is read."""
+
+    __slots__ = ("array",)
+
+    def __init__(self, array: np.ndarray):
+        self.array = array
+
+    def __len__(self):
+        return len(self.array)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[k] for k in range(*i.indices(len(self)))]
+        row = self.array[i]
+        return {k: row[k].item() for k in _RESULT_KEYS}
+
+    def column(self, key: str) -> np.ndarray:
+        return self.array[key]
+
+    def __eq__(self, other):  # as the list of dicts
+        if isinstance(other, Results):
+            return list(self) == list(other)
+        if isinstance(other, list):
+            return list(self) == other
+        return NotImplemented
+
+    __hash__ = None
+
+
+def _sizes(v) -> np.ndarray:
+    """Pair sizes as a contiguous int64 array (passed to the library by address)."""
+    return np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+
+
+def _results(P: int):
+    arr = np.zeros(P, dtype=RESULT_DTYPE)
+    return arr, arr.ctypes.data_as(C.POINTER(hb_result))
 
 
 _lib = None
@@ -215,20 +270,19 @@ def hb_perm_test(ctx: Context, X: torch.Tensor, Y: torch.Tensor, opts: hb_opts, 
 
 def hb_perm_test_batched(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, stream=None, check=True):
     """XY packs, per pair, n[p] rows of X then m[p] rows of Y (device or host
-    tensor).  Returns a list of result dicts."""
+    tensor).  Returns a Results sequence: one result dict per pair."""
     dt = _dtype_code(XY)
     d = XY.shape[1]
     if not XY.is_contiguous():
         raise ValueError("expected a contiguous tensor")
-    P = len(n)
-    na = (C.c_int64 * P)(*[int(v) for v in n])
-    ma = (C.c_int64 * P)(*[int(v) for v in m])
-    res = (hb_result * P)()
-    st = lib().hb_perm_test_batched(ctx.handle, P, C.c_void_p(XY.data_ptr()), na, ma, d, dt, C.byref(opts), res,
-                                    _stream(stream))
+    na, ma = _sizes(n), _sizes(m)
+    P = len(na)
+    arr, res = _results(P)
+    st = lib().hb_perm_test_batched(ctx.handle, P, C.c_void_p(XY.data_ptr()), na.ctypes.data, ma.ctypes.data, d, dt,
+                                    C.byref(opts), res, _stream(stream))
     if check:
         _check(st)
-    return [r.as_dict() for r in res]
+    return Results(arr)
 
 
 class Plan:
@@ -239,10 +293,9 @@ class Plan:
         self.P = len(n)
         self.d = int(d)
         self.dtype = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
-        na = (C.c_int64 * self.P)(*[int(v) for v in n])
-        ma = (C.c_int64 * self.P)(*[int(v) for v in m])
+        na, ma = _sizes(n), _sizes(m)
         h = C.c_void_p()
-        _check(lib().hb_plan_create(ctx.handle, self.P, na, ma, self.d, self.dtype, C.byref(opts), C.byref(h)))
+        _check(lib().hb_plan_create(ctx.handle, self.P, na.ctypes.data, ma.ctypes.data, self.d, self.dtype, C.byref(opts), C.byref(h)))
         self._h = h
         self._ctx = ctx  # the plan keeps the context alive
 
@@ -251,11 +304,11 @@ class Plan:
             raise ValueError("expected a contiguous tensor")
         if XY.shape[1] != self.d or _dtype_code(XY) != self.dtype:
             raise ValueError("XY does not match the plan's d / dtype")
-        res = (hb_result * self.P)()
+        arr, res = _results(self.P)
         st = lib().hb_plan_execute(self._h, C.c_void_p(XY.data_ptr()), res, _stream(stream))
         if check:
             _check(st)
-        return [r.as_dict() for r in res]
+        return Results(arr)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -338,8 +391,8 @@ class hb_mlp(C.Structure):
 
 
 def _batched_args(XY, n, m):
-    P = len(n)
-    return P, (C.c_int64 * P)(*[int(v) for v in n]), (C.c_int64 * P)(*[int(v) for v in m])
+    na, ma = _sizes(n), _sizes(m)
+    return len(na), (C.c_int64 * len(na)).from_buffer(na), (C.c_int64 * len(ma)).from_buffer(ma)
 
 
 def triage_features(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, stream=None):

@@ -55,3 +55,26 @@ def test_binding_refuses_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(H, "_lib", None)
     with pytest.raises(RuntimeError):
         H.lib()
+
+
+def test_results_array_mirrors_hb_result():
+    """The structured numpy type of batched results has hb_result's layout,
+    and Results gives the same dicts as hb_result.as_dict on the same bytes."""
+    assert H.RESULT_DTYPE.itemsize == ctypes.sizeof(H.hb_result)
+    for k, _ in H.hb_result._fields_:
+        assert H.RESULT_DTYPE.fields[k][1] == getattr(H.hb_result, k).offset
+    arr = H.np.zeros(3, dtype=H.RESULT_DTYPE)
+    arr["p"] = [0.5, 0.25, 1.0]
+    arr["count"] = [4, 7, 2**40]
+    arr["status"] = [0, 3, -1]
+    arr["band_max"] = [1e-9, 0.0, 2.5]
+    view = (H.hb_result * 3).from_buffer(arr)
+    res = H.Results(arr)
+    assert len(res) == 3
+    assert [r for r in res] == [v.as_dict() for v in view]
+    assert res[1:] == [view[1].as_dict(), view[2].as_dict()]
+    assert list(res.column("count")) == [4, 7, 2**40]
+    assert res == H.Results(arr.copy()) and res == [v.as_dict() for v in view]
+    other = arr.copy()
+    other["count"][2] += 1
+    assert res != H.Results(other)
