@@ -422,6 +422,215 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
     }
 }
 
+// The same outputs for the tensor-core path on BF16 storage with two slices
+// and d a multiple of 8, with lanes along tokens.  Warp w takes the 8-column
+// groups w, w + 8, ... ; lane l takes the four consecutive token positions
+// 4l .. 4l + 3 of the chunk, position q being token tok0 - g + q with
+// g = tok0 mod 4, so that a lane's four values of one slice column leave in
+// one aligned 8-byte store (the host keeps g + nrows <= 128).  Where an
+// element's slices are exact (residual 0), its value hi q_hi + lo q_lo enters
+// the column total through integer sums of hi and lo (a warp reduction per
+// column); the few other elements are added exactly as values, with the same
+// rule as the oracle (|v| < 2^-64 counts as 0), so every chunk total is the
+// exact sum of its values.
+__device__ __forceinline__ i128 warp_sum_i128(i128 v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const u128 u = (u128)v;
+        const uint32_t w0 = __shfl_xor_sync(0xffffffffu, (uint32_t)u, off);
+        const uint32_t w1 = __shfl_xor_sync(0xffffffffu, (uint32_t)(u >> 32), off);
+        const uint32_t w2 = __shfl_xor_sync(0xffffffffu, (uint32_t)(u >> 64), off);
+        const uint32_t w3 = __shfl_xor_sync(0xffffffffu, (uint32_t)(u >> 96), off);
+        v += (i128)(((u128)w3 << 96) | ((u128)w2 << 64) | ((u128)w1 << 32) | (u128)w0);
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_ru(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// Exact fixed-point value (unit 2^-87) of a residual of the split: a nonzero
+// residual of a value z >= 2^-64 is a multiple of z's last bit, so >= 2^-71
+// and a multiple of 2^-87 (the right shift below drops only zero bits).
+__device__ __forceinline__ i128 fixed_from_residual(uint32_t b)
+{
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0;
+    const uint64_t mant = (b & 0x7fffffu) | 0x800000u;
+    const u128 m = e >= 63u ? (u128)mant << (e - 63u) : (u128)(mant >> min(63u - e, 63u));
+    return (b >> 31) ? -(i128)m : (i128)m;
+}
+
+// The exact part of one column of a warp's 128 positions, called by the whole
+// warp (out of line: rare).  Split columns (fast): the residuals of the values
+// >= 2^-64 exactly (q_hi hi + q_lo lo are already in the integer sums);
+// otherwise every value exactly (|v| < 2^-64 counts as 0, as in the oracle).
+// Both sum the residuals rounded up.
+struct SlowCol {
+    i128 sum;
+    float ca;
+};
+
+__device__ __noinline__ SlowCol zs_slow_column(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, bool high,
+                                               unsigned int okm, bool fast, float inv, float qh, float inv_l,
+                                               float ql)
+{
+    i128 sl = 0;
+    float ca = 0.0f;
+    const uint32_t ws[4] = {w0, w1, w2, w3};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!((okm >> i) & 1u)) continue;
+        const uint32_t bb = high ? (ws[i] & 0xffff0000u) : (ws[i] << 16);
+        const float z = __uint_as_float(bb);
+        const float hi = rintf(__fmul_rn(z, inv));
+        const float w = __fmaf_rn(-hi, qh, z);
+        const float lo = rintf(__fmul_rn(w, inv_l));
+        const float res = __fmaf_rn(-lo, ql, w);
+        if (!fast) sl += fixed_from_f32bits(bb);
+        else if (res != 0.0f && ((bb >> 23) & 0xffu) >= 63u) sl += fixed_from_residual(__float_as_uint(res));
+        ca = __fadd_ru(ca, fabsf(res));
+    }
+    SlowCol r;
+    r.sum = warp_sum_i128(sl);
+    r.ca = warp_sum_ru(ca);
+    return r;
+}
+
+__global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restrict__ meta,
+                                                    const RowChunk *__restrict__ chunks, const RunOpts o,
+                                                    const PairState *__restrict__ st, const uint4 *__restrict__ Z,
+                                                    const unsigned int *__restrict__ colmax,
+                                                    i128 *__restrict__ tpart, float *__restrict__ cpart,
+                                                    unsigned short *__restrict__ zq, int64_t zq_ld)
+{
+    const RowChunk ch = chunks[blockIdx.x];
+    const PairMeta pm = meta[ch.pair];
+    if (st[ch.pair].status != ST_OK) return;
+    const int d = o.d, cw = o.cw;
+    const int64_t tok0 = (ch.side ? pm.n : 0) + ch.row0;  // token index within the pair
+    const int g = (int)(tok0 & 3);
+    const bool last = ch.side == 1 && ch.row0 + ch.nrows == pm.m;
+    const int npad = last ? pm.N_pad - pm.N : 0;
+    const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const int rb = 4 * ln - g;  // chunk row of the lane's first position
+    bool ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ok[i] = rb + i >= 0 && rb + i < ch.nrows;
+    const bool full = ok[0] && ok[1] && ok[2] && ok[3];
+    const unsigned int okm = (ok[0] ? 1u : 0u) | (ok[1] ? 2u : 0u) | (ok[2] ? 4u : 0u) | (ok[3] ? 8u : 0u);
+    const int64_t tq = pm.z_row + tok0 - g + 4 * ln;  // slice-row offset of the lane's first position
+    const unsigned int *cm = colmax + (int64_t)ch.pair * o.d_pad;
+    const int d16 = d / 8;  // 16-byte units per row
+    // row rb of the chunk (the lane's first position) in 16-byte units; only rows
+    // with ok[i] are read
+    const int64_t zr = (pm.z_row + tok0 + rb) * d16;
+    const int lcw = __ffs(cw) - 1;  // cw is a power of two
+
+    for (int c8 = wp; c8 < d16; c8 += 8) {
+        const int j = 8 * c8;
+        uint4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = ok[i] ? __ldg(Z + zr + i * d16 + c8) : make_uint4(0u, 0u, 0u, 0u);
+        // the 8 columns lie in one tile of cw columns: slice s of column j + e is row base + s cw + e
+        const int64_t base = ((int64_t)(j >> lcw) << (lcw + 1)) + (j & (cw - 1));
+        unsigned short *dh = zq + base * zq_ld + tq;
+        unsigned short *dl = dh + ((int64_t)zq_ld << lcw);
+        // lane e < 8 keeps column j + e's reductions for the group's epilogue
+        int my_ih = 0, my_il = 0, my_E = 0;
+        bool my_fast = false;
+        i128 my_slow = 0;
+        float my_ca = 0.0f;
+        const uint4 m0 = __ldg(reinterpret_cast<const uint4 *>(cm + j));
+        const uint4 m1 = __ldg(reinterpret_cast<const uint4 *>(cm + j) + 1);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const unsigned int mb = e == 0 ? m0.x : e == 1 ? m0.y : e == 2 ? m0.z : e == 3 ? m0.w
+                                  : e == 4 ? m1.x : e == 5 ? m1.y : e == 6 ? m1.z : m1.w;
+            const int E = col_bound_exp(mb);
+            // split range: q_hi = 2^(E-8), its reciprocal and q_lo = q_hi/512 normal FP32
+            // numbers (always so for valid inputs unless the column is all zero or below
+            // 2^-100); integer sums: residual-free values are then >= 2^-64 or 0
+            const bool split = mb != 0u && E >= -100 && E <= 100;
+            const bool fast = split && E >= -46;
+            // outside the split range the slices are 0 (reciprocals 0) and the residual is z
+            const int Es = split ? E : 8;
+            const float qh = __int_as_float((Es - 8 + 127) << 23), ql = qh * (1.0f / 512.0f);
+            const float inv = split ? __int_as_float((127 - (Es - 8)) << 23) : 0.0f, inv_l = inv * 512.0f;
+            float hf[4], lf[4];
+            float shi = 0.0f, slo = 0.0f, racc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t wd = (e >> 1) == 0 ? v[i].x : (e >> 1) == 1 ? v[i].y : (e >> 1) == 2 ? v[i].z : v[i].w;
+                const float z = __uint_as_float((e & 1) ? (wd & 0xffff0000u) : (wd << 16));  // 0 where !ok
+                // exact steps: power-of-two scalings and exact remainders
+                hf[i] = rintf(__fmul_rn(z, inv));
+                const float w = __fmaf_rn(-hf[i], qh, z);
+                lf[i] = rintf(__fmul_rn(w, inv_l));
+                const float res = __fmaf_rn(-lf[i], ql, w);
+                shi += hf[i];  // exact: integers, |sum| <= 1024
+                slo += lf[i];
+                racc += fabsf(res);  // 0 iff every residual is 0
+            }
+            // hi and lo are integers of magnitude <= 256: the high halves of their FP32 bits
+            // are their BF16 bits
+            const uint32_t hp0 = __byte_perm(__float_as_uint(hf[0]), __float_as_uint(hf[1]), 0x7632);
+            const uint32_t hp1 = __byte_perm(__float_as_uint(hf[2]), __float_as_uint(hf[3]), 0x7632);
+            const uint32_t lp0 = __byte_perm(__float_as_uint(lf[0]), __float_as_uint(lf[1]), 0x7632);
+            const uint32_t lp1 = __byte_perm(__float_as_uint(lf[2]), __float_as_uint(lf[3]), 0x7632);
+            if (full) {
+                *reinterpret_cast<uint2 *>(dh) = make_uint2(hp0, hp1);
+                *reinterpret_cast<uint2 *>(dl) = make_uint2(lp0, lp1);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (ok[i]) {
+                        const uint32_t hp = i < 2 ? hp0 : hp1, lp = i < 2 ? lp0 : lp1;
+                        dh[i] = (unsigned short)((i & 1) ? hp >> 16 : hp);
+                        dl[i] = (unsigned short)((i & 1) ? lp >> 16 : lp);
+                    }
+            }
+            dh += zq_ld;
+            dl += zq_ld;
+            const int ih = __reduce_add_sync(0xffffffffu, __float2int_rz(shi));
+            const int il = __reduce_add_sync(0xffffffffu, __float2int_rz(slo));
+            if (ln == e) {
+                my_ih = ih;
+                my_il = il;
+                my_E = E;
+                my_fast = fast;
+            }
+            if (__any_sync(0xffffffffu, !fast || racc != 0.0f)) {
+                const uint32_t w0 = (e >> 1) == 0 ? v[0].x : (e >> 1) == 1 ? v[0].y : (e >> 1) == 2 ? v[0].z : v[0].w;
+                const uint32_t w1 = (e >> 1) == 0 ? v[1].x : (e >> 1) == 1 ? v[1].y : (e >> 1) == 2 ? v[1].z : v[1].w;
+                const uint32_t w2 = (e >> 1) == 0 ? v[2].x : (e >> 1) == 1 ? v[2].y : (e >> 1) == 2 ? v[2].z : v[2].w;
+                const uint32_t w3 = (e >> 1) == 0 ? v[3].x : (e >> 1) == 1 ? v[3].y : (e >> 1) == 2 ? v[3].z : v[3].w;
+                const SlowCol sc = zs_slow_column(w0, w1, w2, w3, (e & 1) != 0, okm, fast, inv, qh, inv_l, ql);
+                if (ln == e) {
+                    my_slow = sc.sum;
+                    my_ca = sc.ca;
+                }
+            }
+        }
+        if (ln < 8) {
+            i128 tot = my_slow;
+            if (my_fast) tot += ((i128)my_ih << (my_E + 79)) + ((i128)my_il << (my_E + 70));
+            tpart[(int64_t)blockIdx.x * d + j + ln] = tot;
+            cpart[(int64_t)blockIdx.x * d + j + ln] = my_ca;
+        }
+        // the last chunk of the pair also zero-fills the padded tokens of the slices
+        for (int k = ln; k < 16 * npad; k += 32) {
+            const int e = k / (2 * npad), s = (k / npad) & 1, t = k % npad;
+            zq[(base + s * cw + e) * zq_ld + pm.z_row + pm.N + t] = 0;
+        }
+    }
+}
+
 // Per (pair, column): exact totals, observed group-1 sums, band constants.
 __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int P, const RunOpts o,
                                 const PairState *__restrict__ st, const unsigned int *__restrict__ colmax,
@@ -552,10 +761,14 @@ void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, 
 
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
-                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, cudaStream_t st)
+                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
+                   cudaStream_t st)
 {
     if (o.dtype == DT_F32)
         k_zstats_partial<DT_F32><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+    else if (tok_layout)
+        k_zstats_tok<<<nch, 256, 0, st>>>(meta, chunks, o, pst, static_cast<const uint4 *>(Z), colmax, tpart, cpart,
+                                          zq, zq_ld);
     else
         k_zstats_partial<DT_BF16><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
     k_zstats_reduce<<<cdiv_((int64_t)P * o.d_pad, 256), 256, 0, st>>>(meta, P, o, pst, colmax, tpart, cpart, t_ex,

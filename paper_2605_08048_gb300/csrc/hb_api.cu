@@ -366,8 +366,13 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int64_t r = 0; r < np; r += CHUNK_ROWS)
             pl.chunks.push_back(RowChunk{(int)p, 0, (int)r, (int)std::min<int64_t>(CHUNK_ROWS, np - r)});
         pm.nchunk_x = (int)pl.chunks.size() - pm.chunk0;
-        for (int64_t r = 0; r < mp; r += CHUNK_ROWS)
-            pl.chunks.push_back(RowChunk{(int)p, 1, (int)r, (int)std::min<int64_t>(CHUNK_ROWS, mp - r)});
+        // the first Y chunk ends where token n + rows is a multiple of 4: every
+        // chunk then starts at a token index t with (t mod 4) + rows <= 128
+        for (int64_t r = 0; r < mp;) {
+            const int64_t rows = std::min<int64_t>(r == 0 ? CHUNK_ROWS - (np & 3) : CHUNK_ROWS, mp - r);
+            pl.chunks.push_back(RowChunk{(int)p, 1, (int)r, (int)rows});
+            r += rows;
+        }
         pm.nchunk_y = (int)pl.chunks.size() - pm.chunk0 - pm.nchunk_x;
         pl.max_Bpad = std::max(pl.max_Bpad, pm.B_pad);
         pl.max_W = std::max(pl.max_W, pm.W);
@@ -591,7 +596,10 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     // step 4: Z statistics, fixed-point slices, T_obs
     const int64_t zq_ld = pl.total_rows_pad;
     xmark(ex, 1);
+    // lanes-along-tokens slices: tensor-core path, two BF16 slices, 16-byte rows
+    const bool tok_layout = mixed && o.slices == 2 && d % 8 == 0;
     launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o, b.cc,
+                  tok_layout,
                   s);
     launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
     CK(cudaGetLastError());

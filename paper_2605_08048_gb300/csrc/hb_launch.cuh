@@ -17,7 +17,8 @@ void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, 
                     const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st);
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
-                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, cudaStream_t st);
+                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
+                   cudaStream_t st);
 void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
                  const ColConst *cc, PairState *pst, cudaStream_t st);
 void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
