@@ -65,6 +65,105 @@ __global__ void __launch_bounds__(256) k_recheck_sums(const PairMeta *__restrict
     out[d + j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - acc);
 }
 
+// The same sums for BF16 storage, d a multiple of 8 and d <= 1024, one block
+// per item.  Warp 0 lists the selected rows of a window of up to RC_WIN_WORDS
+// label words in shared memory; thread t < G = d/8 sums the 16-byte column
+// group t (8 columns) over the listed rows of even index, thread G + t over
+// those of odd index (four loads in flight each), and after the last window
+// the two exact halves are added through shared memory.
+constexpr int RC_WIN_WORDS = 256;  // 8192 rows per window
+constexpr int RC_MAX_G = 128;      // d <= 1024
+
+__global__ void __launch_bounds__(256) k_recheck_rows(const PairMeta *__restrict__ meta, const RunOpts o,
+                                                      const uint4 *__restrict__ Z, const i128 *__restrict__ t_ex,
+                                                      const unsigned int *__restrict__ colmax,
+                                                      const uint32_t *__restrict__ bits,
+                                                      const RecheckItem *__restrict__ list,
+                                                      const unsigned int *__restrict__ n_items, unsigned int cap,
+                                                      unsigned int batch0, double *__restrict__ sums)
+{
+    __shared__ uint16_t rows[RC_WIN_WORDS * 32];
+    __shared__ i128 half1[RC_MAX_G * 8];
+    __shared__ int nsel;
+    const unsigned int total = min(*n_items, cap);
+    const unsigned int it = batch0 + blockIdx.x;
+    if (it >= total) return;
+    const int d = o.d, G = d / 8;
+    const RecheckItem item = list[it];
+    const PairMeta pm = meta[item.pair];
+    const int lane = threadIdx.x & 31;
+    const int h = (int)threadIdx.x >= G ? 1 : 0, gg = (int)threadIdx.x - h * G;
+    const bool live = gg < G;  // blockDim.x may exceed 2G (whole warps)
+    WinAcc wa[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        wa[e].init(live ? col_bound_exp(colmax[(int64_t)item.pair * o.d_pad + 8 * gg + e]) : 0);
+    int cnt = 0;
+    for (int w0 = 0; w0 < pm.W; w0 += RC_WIN_WORDS) {
+        const int nw = min(RC_WIN_WORDS, pm.W - w0);
+        __syncthreads();  // the previous window's list is consumed
+        if (threadIdx.x < 32) {
+            int base = 0;
+            for (int k0 = 0; k0 < nw; k0 += 32) {
+                const int k = k0 + lane;
+                uint32_t word = k < nw ? bits[pm.lab_off + (int64_t)(w0 + k) * pm.B_pad + item.b] : 0u;
+                const int c = __popc(word);
+                int incl = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                int pos = base + incl - c;
+                while (word) {
+                    rows[pos++] = (uint16_t)(k * 32 + __ffs(word) - 1);
+                    word &= word - 1u;
+                }
+                base += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) nsel = base;
+        }
+        __syncthreads();
+        const int ns = nsel;
+        if (!live) continue;
+        const uint4 *zp = Z + (pm.z_row + (int64_t)w0 * 32) * G + gg;
+        for (int r0 = h; r0 < ns; r0 += 8) {
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                v[k] = r0 + 2 * k < ns ? __ldg(zp + (int64_t)rows[r0 + 2 * k] * G) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t wv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) wa[e].add((e & 1) ? (wv[e >> 1] & 0xffff0000u) : (wv[e >> 1] << 16));
+            }
+            if ((++cnt & 31) == 0) {  // at least every 128 adds
+#pragma unroll
+                for (int e = 0; e < 8; ++e) wa[e].flush();
+            }
+        }
+    }
+    i128 acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = wa[e].total();
+    if (live && h == 1) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) half1[gg * 8 + e] = acc[e];
+    }
+    __syncthreads();
+    if (live && h == 0) {
+        double *out = sums + (int64_t)blockIdx.x * 2 * d;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = 8 * gg + e;
+            const i128 a = acc[e] + half1[gg * 8 + e];
+            out[j] = fixed_to_f64(a);
+            out[d + j] = fixed_to_f64(t_ex[(int64_t)item.pair * d + j] - a);
+        }
+    }
+}
+
 // Stage 2: squared norms as sequential FMA chains over j = 0..d-1 (two
 // threads per item, one per group, all items in flight together), then the
 // exact decision with correctly rounded IEEE operations only.
@@ -133,8 +232,13 @@ void launch_recheck(unsigned int cap, unsigned int batch, int max_W, const PairM
     // batches up to the list capacity; batches past the actual count exit at once
     const size_t smem = sizeof(uint32_t) * (size_t)max_W;
     const dim3 g1(batch, (unsigned)((o.d + 255) / 256));
+    const bool rows_path = o.dtype == DT_BF16 && o.d % 8 == 0 && o.d <= 8 * RC_MAX_G;
+    const unsigned int rthreads = (unsigned)(((2 * (o.d / 8) + 31) / 32) * 32);
     for (unsigned int b0 = 0; b0 < cap; b0 += batch) {
-        if (o.dtype == DT_F32)
+        if (rows_path)
+            k_recheck_rows<<<batch, rthreads, 0, st>>>(meta, o, static_cast<const uint4 *>(Z), t_ex, colmax, bits,
+                                                       list, n_items, cap, b0, sums);
+        else if (o.dtype == DT_F32)
             k_recheck_sums<DT_F32><<<g1, 256, smem, st>>>(meta, o, Z, t_ex, colmax, bits, list, n_items, cap, b0,
                                                           sums);
         else
