@@ -51,8 +51,10 @@ __device__ __forceinline__ void walk_labels(const LabelKeys &K, int n, int N, ui
         uint4 c = make_uint4(y0, y1, __umulhi(M0, q) ^ bhi ^ rk1[0], M0 * q);
 #pragma unroll
         for (int r = 1; r < 10; ++r) {
-            const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
-            const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+            // one widening multiply gives both halves of each product
+            const uint64_t p0 = (uint64_t)M0 * c.x, p1 = (uint64_t)M1 * c.z;
+            const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+            const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
             c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
         }
         return c;
@@ -61,8 +63,35 @@ __device__ __forceinline__ void walk_labels(const LabelKeys &K, int n, int N, ui
     uint32_t word = 0;
     int i = 0;
     bool forced = false;  // the rest is all group 2 (need = 0) or all group 1
-    // full groups of four positions
-    for (; i + 4 <= N; i += 4) {
+    // full words of 32 positions: eight groups of four, the forced test once per word
+    for (; i + 32 <= N; i += 32) {
+        if (need == 0u || need == (uint32_t)(N - i)) {
+            forced = true;
+            break;
+        }
+        uint32_t rem = (uint32_t)(N - i);
+        uint32_t wd = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const uint4 w = draw((uint32_t)((i >> 2) + g));
+            uint32_t t = __umulhi(w.x, rem) < need;
+            need -= t;
+            wd |= t << (4 * g);
+            t = __umulhi(w.y, rem - 1u) < need;
+            need -= t;
+            wd |= t << (4 * g + 1);
+            t = __umulhi(w.z, rem - 2u) < need;
+            need -= t;
+            wd |= t << (4 * g + 2);
+            t = __umulhi(w.w, rem - 3u) < need;
+            need -= t;
+            wd |= t << (4 * g + 3);
+            rem -= 4u;
+        }
+        emit(i >> 5, wd);
+    }
+    // full groups of four positions of the last, partial word
+    for (; !forced && i + 4 <= N; i += 4) {
         if (need == 0u || need == (uint32_t)(N - i)) {
             forced = true;
             break;

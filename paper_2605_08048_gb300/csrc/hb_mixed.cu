@@ -48,7 +48,8 @@ constexpr int MX_NS = 4;             // pipeline stages
 constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
 constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB
 constexpr int MX_STAGE_BYTES = 48 * 1024;         // A + up to 256 B-rows x 128 B
-constexpr int MX_APROD = 8;         // A-producer warps: two per row block, one label word each
+constexpr int MX_APROD = 8;         // A-producer warps (8: two per row block, one label word each; or 4)
+static_assert(MX_APROD == 8 || MX_APROD == 4, "four or eight A producers");
 constexpr int MX_THREADS = 192 + 32 * MX_APROD;
 constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of 256 columns
 constexpr int MX_BAR_OFF = MX_NS * MX_STAGE_BYTES;
@@ -571,7 +572,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
         // ---------------- A producers: label bits -> BF16 0/1 ----------------
         const int pi = warp - 6;
         const int r = (pi & 3) * 32 + lane;  // relabelling row of the tile, 0..127
-        const int half = pi >> 2;            // tokens 32*half .. 32*half+31 of each stage
+        // with eight producers a warp fills one 32-token half of each stage, with
+        // four it fills both
+        constexpr int HALVES = 8 / MX_APROD;
+        const int half0 = MX_APROD == 8 ? (pi >> 2) : 0;
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -582,18 +586,19 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
             const int KC = pm.N_pad / MX_K;
             const int tile = w.tile * MIXED_CLUSTER + (int)crank;
             const uint32_t *lab = P.bits + pm.lab_off + (int64_t)tile * MX_M + r;
-            // this warp's label word of K-chunk kc (identical for every column tile)
-            auto word = [&](int kc) {
-                const int w0 = 2 * kc + half;
+            // this warp's label word of K-chunk kc and half h (identical for every column tile)
+            auto word = [&](int kc, int h) {
+                const int w0 = 2 * kc + half0 + h;
                 return w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
             };
             // loads run MX_PF stages ahead of the expansion (a register ring,
             // wrapping across column tiles), which covers the DRAM latency
-            uint32_t rw[MX_PF];
+            uint32_t rw[HALVES][MX_PF];
             int knext = 0;  // K-chunk of the next load
 #pragma unroll
             for (int i = 0; i < MX_PF; ++i) {
-                rw[i] = word(knext);
+#pragma unroll
+                for (int h = 0; h < HALVES; ++h) rw[h][i] = word(knext, h);
                 if (++knext == KC) knext = 0;
             }
             for (int c = 0; c < C && ok; ++c) {
@@ -603,23 +608,27 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                         ok = false;
                         break;
                     }
-                    const uint32_t wd = rw[0];
-#pragma unroll
-                    for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
-                    rw[MX_PF - 1] = word(knext);
-                    if (++knext == KC) knext = 0;
                     uint8_t *row = smem + stage * STAGE + r * 128;
 #pragma unroll
-                    for (int cl = 0; cl < 4; ++cl) {
-                        const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
-                        const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
-                        uint4 v;
-                        v.x = expand2(b8);
-                        v.y = expand2(b8 >> 2);
-                        v.z = expand2(b8 >> 4);
-                        v.w = expand2(b8 >> 6);
-                        *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
+                    for (int h = 0; h < HALVES; ++h) {
+                        const uint32_t wd = rw[h][0];
+#pragma unroll
+                        for (int i = 0; i + 1 < MX_PF; ++i) rw[h][i] = rw[h][i + 1];
+                        rw[h][MX_PF - 1] = word(knext, h);
+                        const int half = half0 + h;
+#pragma unroll
+                        for (int cl = 0; cl < 4; ++cl) {
+                            const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
+                            const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
+                            uint4 v;
+                            v.x = expand2(b8);
+                            v.y = expand2(b8 >> 2);
+                            v.z = expand2(b8 >> 4);
+                            v.w = expand2(b8 >> 6);
+                            *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
+                        }
                     }
+                    if (++knext == KC) knext = 0;
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full_a(stage));
