@@ -150,6 +150,36 @@ def test_exhaustive_parity(ctx, path, n, m, stat):
     assert res["B_eff"] == math.comb(n + m, n)
 
 
+def _edge_columns(X, Y):
+    """Columns that take the exact side paths of the Z statistics and of the
+    reflection: an all-zero column, one scaled by 2^-60 (partly below 2^-64,
+    which counts as 0), one scaled by 1e-35 (no fixed-point split; reflected
+    values that small take the FP64 expression), and normal columns with a few
+    entries of 3e-8 (nonzero residuals of the split) or 1e-21 (below 2^-64)."""
+    out = []
+    for A in (X, Y):
+        F = synth.bf16_bits_to_f32(A).copy()
+        F[:, 3] = 0.0
+        F[:, 5] *= np.float32(2.0 ** -60)
+        F[:, 9] *= np.float32(1e-35)
+        F[::17, 7] = np.float32(3e-8)
+        F[1::13, 11] = np.float32(-1e-21)
+        out.append(synth.to_bf16_bits(F))
+    return out[0], out[1]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_columns_parity(ctx, path):
+    X, Y = _edge_columns(*synth.pair(77, 150, 170, 64, 0.35, 0.385, None, "bf16"))
+    st, Zw, _, _, _ = O.align(X, Y)
+    Z, _, _ = H.hb_align(ctx, dev(X), dev(Y))
+    assert st == O.OK and (host(Z) == Zw).all()
+    o = O.opts(B=999, seed=6)
+    ref, Tref, _ = O.perm_test(X, Y, o, want_T=True)
+    res, T = H.hb_perm_test(ctx, dev(X), dev(Y), H.make_opts(B=999, seed=6, path=path), want_T=True)
+    _compare(res, T, ref, Tref, O.STAT_LOGVOL_VMF)
+
+
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("align,side", [(0, 0), (1, 1)])
 def test_naive_and_reflect_y_parity(ctx, path, align, side):
