@@ -51,6 +51,13 @@ constexpr int MX_STAGE_BYTES = 48 * 1024;         // A + up to 256 B-rows x 128 
 constexpr int MX_APROD = 8;         // A-producer warps (8: two per row block, one label word each; or 4)
 static_assert(MX_APROD == 8 || MX_APROD == 4, "four or eight A producers");
 constexpr int MX_THREADS = 192 + 32 * MX_APROD;
+// The launch bound names more threads than a CTA has, which caps the kernel at
+// 96 registers a thread (65536 / 576 rounded down): the SM then keeps about a
+// third of its registers free for the label draws, which run beside the GEMM
+// on another stream and finish under it instead of in the gaps between its
+// launches.
+constexpr int MX_BOUND_THREADS = 576;
+static_assert(MX_BOUND_THREADS >= MX_THREADS, "launch bound");
 constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of 256 columns
 constexpr int MX_BAR_OFF = MX_NS * MX_STAGE_BYTES;
 constexpr int MX_CONST_OFF = MX_BAR_OFF + 256;
@@ -317,6 +324,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
@@ -348,7 +364,7 @@ __device__ __forceinline__ uint32_t expand2(uint32_t b)
 // the kernel
 // ---------------------------------------------------------------------------
 template <int S, int CW, int CG>
-__global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
+__global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
     // CW z-columns per column tile: 128 (wide) or 64 (narrow) for two slices,
     // 64 or 32 for three.  CG = 2: CTA pairs (ranks 2k, 2k+1) run M = 256 MMAs,
@@ -671,18 +687,21 @@ __global__ void __launch_bounds__(MX_THREADS, 1) k_mixed(const __grid_constant__
                 }
                 tc_fence_after();
                 const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)abuf * 256u;
+                // 16 accumulator columns per TMEM load keep the epilogue within the
+                // kernel's register budget (the label draws run beside the GEMM in
+                // the registers it leaves free)
 #pragma unroll 1
-                for (int ch = 0; ch < CW / 32; ++ch) {
-                    uint32_t dh[32], dl[32], dl2[32];
-                    tmem_ld32(tb + ch * 32, dh);
-                    tmem_ld32(tb + CW + ch * 32, dl);
-                    if (S == 3) tmem_ld32(tb + 2 * CW + ch * 32, dl2);
+                for (int ch = 0; ch < CW / 16; ++ch) {
+                    uint32_t dh[16], dl[16], dl2[16];
+                    tmem_ld16(tb + ch * 16, dh);
+                    tmem_ld16(tb + CW + ch * 16, dl);
+                    if (S == 3) tmem_ld16(tb + 2 * CW + ch * 16, dl2);
                     tmem_ld_wait();
                     float pq1[4] = {0.f, 0.f, 0.f, 0.f}, pq2[4] = {0.f, 0.f, 0.f, 0.f};
                     float pe1[4] = {0.f, 0.f, 0.f, 0.f}, pe2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float4 k = consts[ch * 32 + i];
+                    for (int i = 0; i < 16; ++i) {
+                        const float4 k = consts[ch * 16 + i];
                         // sigma_1 = q_hi*D_hi + q_lo*D_lo (+ q_lo2*D_lo2): exact products, one rounding each
                         float s1 = __fmul_rn(__uint_as_float(dh[i]), k.x);
                         s1 = __fmaf_rn(__uint_as_float(dl[i]), k.x * (1.0f / 512.0f), s1);
