@@ -236,8 +236,8 @@ struct Plan {
     std::vector<WorkItem> items;  // (pair, 128-relabelling tile), costliest pairs first
     int64_t total_rows_pad = 0, total_label_words = 0, total_B = 0;
     int max_Bpad = 0, max_W = 0, max_N = 0;
-    // mixed path: pairs in the items' order, cut into nlc chunks of about
-    // equal label work; chunk c is pairs order[lc_pair[c] .. lc_pair[c+1]) and
+    // mixed path: pairs in the items' order, cut into nlc chunks of label work
+    // (a smaller first one, the rest even); chunk c is pairs order[lc_pair[c] .. lc_pair[c+1]) and
     // items [lc_item[c], lc_item[c+1]), so its GEMM can start as soon as its
     // labels are drawn while the next chunk's labels are still being drawn
     std::vector<int> order;
@@ -390,7 +390,7 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int p : order)
             if (pl.init_bad[p] == 0)
                 for (int g = 0; g < pl.meta[p].B_pad / (128 * MIXED_CLUSTER); ++g) pl.items.push_back(WorkItem{p, g});
-        // label chunks of about equal label work, in the same order
+        // label chunks in the same order
         pl.order = order;
         int64_t total = 0;
         for (int p : order) total += (int64_t)pl.meta[p].W * pl.meta[p].B_pad;
@@ -399,7 +399,11 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         int64_t acc = 0;
         int i = 0;
         for (int c = 1; c < LABEL_CHUNKS; ++c) {
-            const int64_t target = total * c / LABEL_CHUNKS;
+            // the first chunk is smaller (16 % of the label work), so that it is drawn
+            // by the time the alignment stages end; the rest is split evenly and drawn
+            // beside the GEMM of the chunks before it
+            const int64_t first = total * 16 / 100;
+            const int64_t target = first + (total - first) * (c - 1) / (LABEL_CHUNKS - 1);
             while (i < (int)P && acc < target) {
                 acc += (int64_t)pl.meta[order[i]].W * pl.meta[order[i]].B_pad;
                 ++i;
