@@ -176,6 +176,18 @@ __device__ __forceinline__ void store_z(void *Z, int64_t idx, double v)
     else reinterpret_cast<unsigned short *>(Z)[idx] = f64_to_bf16_rn(v);
 }
 
+// The exact FP64 dot product c = u^T x_r of the reference, a sequential FMA
+// chain over j = 0..d-1, for the rare elements a BF16-storage reflection cannot
+// decide from its compensated FP32 evaluation; -2c is kept in shared memory.
+template <int DT>
+__device__ __noinline__ double reflect_chain(const void *src, int64_t row, int d, const double *up)
+{
+    double c = 0.0;
+    for (int j = 0; j < d; ++j)
+        c = __fma_rn(up[j], f32_to_f64(__uint_as_float(load_f32bits(src, DT, row * d + j))), c);
+    return -2.0 * c;  // exact scaling by -2
+}
+
 template <int DT>
 __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
                                                  const RunOpts o, const PairState *__restrict__ st,
@@ -184,8 +196,10 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
 {
     __shared__ float xs[CHUNK_ROWS][RT + 1];
     __shared__ double us[RT];
-    __shared__ double cs[CHUNK_ROWS];
-    __shared__ float cs32[CHUNK_ROWS];
+    __shared__ float uh_s[RT], ul_s[RT];
+    __shared__ double cs[CHUNK_ROWS];      // FP32 storage: -2c per row; BF16: -2c of fallback rows
+    __shared__ float ah_s[CHUNK_ROWS], al_s[CHUNK_ROWS], dl_s[CHUNK_ROWS];
+    __shared__ int chain_s[CHUNK_ROWS];    // BF16: cs[r] holds the exact -2c
     const RowChunk ch = chunks[blockIdx.x];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
@@ -196,8 +210,13 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
     const double *up = u + (int64_t)ch.pair * d;
 
     if (reflect) {
-        // c_r = u^T x_r, sequential FMA chain over j = 0..d-1 (one thread per row)
+        // FP32 storage: c_r = u^T x_r as the sequential FP64 FMA chain.  BF16 storage:
+        // a compensated FP32 dot product instead (u_j = uh + ul + e_j with |e_j| <=
+        // 2^-48 |u_j|; exact products uh x = p + e; the partial sums of p by TwoSum,
+        // their errors, e and ul x summed by a second TwoSum level), with a rigorous
+        // bound of its distance to the FP64 chain (one thread per row)
         double c = 0.0;
+        float fs = 0.0f, fc = 0.0f, fcc = 0.0f, fa = 0.0f;
         for (int j0 = 0; j0 < d; j0 += RT) {
             const int w = min(RT, d - j0);
             // loads in batches of eight in flight before their stores (blockDim.x == 128)
@@ -217,23 +236,66 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
                     xs[t / RT][t % RT] = __uint_as_float(xv[k]);
                 }
             }
-            if (threadIdx.x < RT) us[threadIdx.x] = threadIdx.x < w ? up[j0 + threadIdx.x] : 0.0;
+            if (threadIdx.x < RT) {
+                const double uu = threadIdx.x < w ? up[j0 + threadIdx.x] : 0.0;
+                us[threadIdx.x] = uu;
+                const float h = __double2float_rn(uu);
+                uh_s[threadIdx.x] = h;
+                ul_s[threadIdx.x] = __double2float_rn(__dsub_rn(uu, (double)h));
+            }
             __syncthreads();
             if (threadIdx.x < ch.nrows) {
                 const int r = threadIdx.x;
-                for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], f32_to_f64(xs[r][jj]), c);
+                if (DT == DT_F32) {
+                    for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], f32_to_f64(xs[r][jj]), c);
+                } else {
+                    for (int jj = 0; jj < w; ++jj) {
+                        const float x = xs[r][jj], uh = uh_s[jj];
+                        const float p = __fmul_rn(uh, x);
+                        const float e = __fmaf_rn(uh, x, -p);
+                        const float q = __fmul_rn(ul_s[jj], x);
+                        const float s1 = __fadd_rn(fs, p), bp = __fsub_rn(s1, fs);
+                        const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(s1, bp)), __fsub_rn(p, bp));
+                        fs = s1;
+                        const float wv = __fadd_rn(__fadd_rn(err, e), q);
+                        const float c1 = __fadd_rn(fc, wv), bw = __fsub_rn(c1, fc);
+                        fcc = __fadd_rn(fcc, __fadd_rn(__fsub_rn(fc, __fsub_rn(c1, bw)), __fsub_rn(wv, bw)));
+                        fc = c1;
+                        fa = __fadd_ru(fa, fabsf(p));
+                    }
+                }
             }
             __syncthreads();
         }
-        cs[threadIdx.x] = -2.0 * c;  // exact scaling by -2
-        cs32[threadIdx.x] = __double2float_rn(-2.0 * c);
+        const int r = threadIdx.x;
+        if (DT == DT_F32) {
+            cs[r] = -2.0 * c;  // exact scaling by -2
+        } else {
+            // a = -2 (ah + al) with ah + al = fs + (fc + fcc) (TwoSum); its distance to
+            // -2 c_chain is at most dl = 2 delta:
+            //   delta = A (2^-45 (d + 8) + 2 (d 2^-24)^3) + 2^-100, A = sum |uh x| (rounded up)
+            // which covers the FP32 roundings of the second level, the first-level error
+            // sums, the dropped ul x and e_j terms, |c_chain - u^T x| <= d 2^-53 sum |u x|,
+            // and products below the normal range
+            const float t = __fadd_rn(fc, fcc);
+            const float ah = __fadd_rn(fs, t), bt = __fsub_rn(ah, fs);
+            const float al = __fadd_rn(__fsub_rn(fs, __fsub_rn(ah, bt)), __fsub_rn(t, bt));
+            const float dd = (float)d;
+            const float g3 = __fmul_ru(dd, 0x1p-24f);
+            const float K = __fadd_ru(__fmul_ru(__fadd_ru(dd, 8.0f), 0x1p-45f), __fmul_ru(2.0f, __fmul_ru(g3, __fmul_ru(g3, g3))));
+            ah_s[r] = -2.0f * ah;
+            al_s[r] = -2.0f * al;
+            dl_s[r] = __fmul_ru(2.0f, __fmaf_ru(fa, K, 0x1p-100f));
+            chain_s[r] = 0;
+        }
         __syncthreads();
     }
     // element pass: z = fl_storage(fma(-2c, u_j, x)) or a copy
     constexpr int RB = 8;  // rows whose loads are issued together
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const double uj = reflect ? up[j] : 0.0;
-        const float uj32 = __double2float_rn(uj);
+        const float uh = __double2float_rn(uj), ul = __double2float_rn(__dsub_rn(uj, (double)uh));
+        const float auh = fabsf(uh);
         float mx = 0.0f;
         for (int rb = 0; rb < ch.nrows; rb += RB) {
         uint32_t xv[RB];
@@ -248,20 +310,43 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
             const uint32_t xb = xv[k];
             float zf;
             if (reflect && DT == DT_BF16) {
-                // FP32 enclosure [y - E, y + E] of v = fl64(a u_j + x), a = -2c:
-                // a and u_j rounded to FP32 give |a u_j - a32 u32| <= 2^-23 |a32 u32| (1 + 2^-23),
-                // the FP32 fma adds <= 2^-24 |y|, the FP64 fma <= 2^-53 |v|; E is at least
-                // twice that, so it also covers the roundings of y -/+ E and of E itself.
-                // BF16 rounding is monotone: equal roundings of both ends are the rounding
-                // of v.  Otherwise (or for tiny y) the FP64 expression decides.
+                // v = fl64(a u_j + x), a = -2 c_chain, from the compensated values:
+                // x + (ah + al)(uh + ul) = S + yl = V + t up to 2^-44 (|x| + |P|), plus
+                // |u_j| dl for the distance of ah + al to a and 2^-52 |v| for the FP64
+                // rounding (E).  With m the BF16 midpoint in |V|'s interval, |v| - m =
+                // (|V| - m) +- t +- E and |V| - m is exact: outside +-E (and with E + |t|
+                // under a quarter step) the sign decides the rounding; otherwise (or for
+                // tiny V) the FP64 chain and expression decide.
                 const float x = __uint_as_float(xb);
-                const float a32 = cs32[r];
-                const float y = __fmaf_rn(a32, uj32, x);
-                const float E = __fmaf_rn(__fadd_rn(fabsf(__fmul_rn(a32, uj32)), fabsf(y)), 0x1p-21f, 0x1p-126f);
-                const unsigned short zl = f32_to_bf16_rn_bits(__fsub_rn(y, E));
-                unsigned short zb = zl;
-                if (zl != f32_to_bf16_rn_bits(__fadd_rn(y, E)) || !(fabsf(y) >= 0x1p-100f))
-                    zb = f64_to_bf16_rn(__fma_rn(cs[r], uj, f32_to_f64(x)));
+                const float ah = ah_s[r];
+                const float P = __fmul_rn(ah, uh), Pe = __fmaf_rn(ah, uh, -P);
+                const float cross = __fmaf_rn(ah, ul, __fmul_rn(al_s[r], uh));
+                const float S = __fadd_rn(x, P), bp = __fsub_rn(S, x);
+                const float Se = __fadd_rn(__fsub_rn(x, __fsub_rn(S, bp)), __fsub_rn(P, bp));
+                const float yl = __fadd_rn(Se, __fadd_rn(Pe, cross));
+                // S + yl renormalised (TwoSum) to V + t with |t| <= 2^-24 |V|: under cancellation
+                // yl can span several BF16 steps of the result
+                const float V = __fadd_rn(S, yl), bv = __fsub_rn(V, S);
+                const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(V, bv)), __fsub_rn(yl, bv));
+                const float E = __fmaf_ru(__fadd_ru(fabsf(x), fabsf(P)), 0x1p-43f,
+                                          __fmaf_ru(auh, __fmul_ru(dl_s[r], 1.01f), 0x1p-100f));
+                const float aV = fabsf(V);
+                const uint32_t tr = __float_as_uint(aV) & 0xffff0000u;
+                const float dist = __fadd_rn(__fsub_rn(aV, __uint_as_float(tr | 0x8000u)), V < 0.0f ? -t : t);
+                // a quarter of V's BF16 step: |v| stays between the neighbouring midpoints
+                const float q4 = __uint_as_float((__float_as_uint(aV) & 0x7f800000u) - (9u << 23));
+                unsigned short zb;
+                if (aV >= 0x1p-100f && fabsf(dist) > __fmul_ru(E, 1.0001f) && __fadd_ru(E, fabsf(t)) < q4) {
+                    zb = (unsigned short)(((__float_as_uint(V) & 0x80000000u) | (tr + (dist > 0.0f ? 0x10000u : 0u))) >>
+                                          16);
+                } else {
+                    if (!((volatile int *)chain_s)[r]) {  // another column's thread may be here too
+                        ((volatile double *)cs)[r] = reflect_chain<DT>(src, ch.row0 + r, d, up);
+                        __threadfence_block();
+                        ((volatile int *)chain_s)[r] = 1;
+                    }
+                    zb = f64_to_bf16_rn(__fma_rn(((volatile double *)cs)[r], uj, f32_to_f64(x)));
+                }
                 reinterpret_cast<unsigned short *>(Z)[zi] = zb;
                 zf = __uint_as_float((uint32_t)zb << 16);
             } else if (reflect) {

@@ -72,6 +72,21 @@ def test_align_bit_exact(ctx, dtype, n, m, d, align, side):
     assert (u.cpu().numpy() == uw).all()
 
 
+@pytest.mark.parametrize("sigma,angle,d", [(0.05, 5.0, 768), (0.35, 60.0, 1024), (0.8, 150.0, 768), (0.05, 170.0, 1024)])
+def test_align_bit_exact_stress(ctx, sigma, angle, d):
+    """BF16 reflection over ~3M elements per case, tight to diffuse clouds and
+    near-identical to near-opposite mean directions (many cancellations in
+    x - 2(u.x)u): the compensated FP32 evaluation and its exact fallback give
+    the oracle's bits everywhere."""
+    X, Y = synth.pair(2024 + d, 2000, 1900, d, sigma, sigma * 1.1, angle, "bf16")
+    st, Zw, uw, _, skw = O.align(X, Y)
+    Z, u, sk = H.hb_align(ctx, dev(X), dev(Y))
+    torch.cuda.synchronize()
+    assert st == O.OK and sk == skw
+    assert (u.cpu().numpy() == uw).all()
+    assert (host(Z) == Zw).all()
+
+
 def test_align_skip_when_directions_equal(ctx):
     X, _ = synth.pair(3, 40, 40, 64, 0.35, 0.35, None, "bf16")
     Z, u, sk = H.hb_align(ctx, dev(X), dev(X.copy()))
