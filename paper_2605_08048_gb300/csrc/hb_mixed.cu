@@ -4,7 +4,7 @@
 //
 // GEMM: D[b, c] = sum_i L[b, i] * Zs[i, c]
 //   A = labels L (128 relabellings x 64 tokens per stage), 0/1 in BF16,
-//       expanded from the packed label bits by four producer warps straight
+//       expanded from the packed label bits by the producer warps straight
 //       into the 128-byte-swizzled K-major shared-memory layout;
 //   B = the fixed-point slices of Z (hi, lo[, lo2] of `cw` columns, tokens
 //       contiguous), loaded by TMA with 128-byte swizzle;
@@ -23,7 +23,10 @@
 //              CTA's warp 5 relays its A readiness to the even CTA instead
 //   warps 6-13 A producers (label bits -> BF16 0/1 tiles): warp 6 + i
 //              expands rows 32*(i%4) .. +31, tokens 32*(i/4) .. +31 (one
-//              label word) of every stage
+//              label word) of every stage (with MX_APROD = 4, both words)
+// The kernel is capped at 96 registers a thread (launch bound; the epilogue
+// reads 16 TMEM columns at a time), leaving room for the label draws, which
+// run beside it on another stream.
 // CG = 2 (HB_PATH_MIXED_2SM): the CTAs of each pair of the cluster (ranks 2k,
 // 2k+1) run tcgen05 cta_group::2 MMAs with M = 256; each holds its 128 rows of
 // A and half of the N columns of every B tile, so each SM receives half the B
