@@ -4,13 +4,15 @@
 //       (Sec. 3.1: x_bar = (1/n) sum x_i), inputs validated on the way
 //   k_axis   : mean directions, v = mu_x - mu_y, u = v/||v|| in FP64
 //       (Sec. 3.1 axis equation; skipped when ||v|| <= 2^-27)
-//   k_reflect: x' = x - 2u(u^T x) per row (Eq. householder_fast), FP64
-//       sequential dot then one FMA per element, rounded once to the storage
-//       type; the other cloud is copied; column maxima for the fixed-point
-//       scales of the mixed path
-//   k_zstats_partial / k_zstats_reduce : exact column totals t of Z and the
-//       group-1 sums of the observed split, the band constants, and (mixed
-//       path) the 16/24-bit fixed-point slices of Z, transposed to
+//   k_reflect: x' = x - 2u(u^T x) per row (Eq. householder_fast), defined as
+//       the FP64 sequential dot then one FMA per element, rounded once to the
+//       storage type (BF16 storage: evaluated in compensated FP32 with a
+//       rigorous bound, the FP64 steps deciding what the bound cannot); the
+//       other cloud is copied; column maxima for the fixed-point scales of
+//       the mixed path
+//   k_zstats_partial / k_zstats_tok / k_zstats_reduce : exact column totals t
+//       of Z and the group-1 sums of the observed split, the band constants,
+//       and (mixed path) the 16/24-bit fixed-point slices of Z in
 //       token-contiguous rows for the tensor-core B operand
 //   k_tobs   : observed statistic T_obs from the exact sums (Eq. tobs)
 //

@@ -6,7 +6,9 @@
 // sigma_2 = t - sigma_1 exactly (Sec. 3.2: the two group sums add up to t),
 // each coordinate is rounded once to FP64, the squared norms are sequential
 // FMA chains over j = 0..d-1, and the decision uses only correctly rounded
-// IEEE operations -- the same arithmetic as the FP64 CPU oracle.
+// IEEE operations -- the same arithmetic as the FP64 CPU oracle.  The exact
+// sums come from k_recheck_rows (BF16 storage, d a multiple of 8, d <= 1024:
+// listed selected rows, 16-byte loads) or else from k_recheck_sums.
 #include "hb_launch.cuh"
 
 namespace hb {
