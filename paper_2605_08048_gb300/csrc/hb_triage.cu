@@ -733,6 +733,7 @@ void mlp_forward(const float *params, const unsigned short *wh, int P, const flo
 void mlp_backward(const float *params, const unsigned short *wh, int P, const float *feat, const float *target,
                   float *work, float *grad, float *loss, cudaStream_t s)
 {
+    (void)params;  // the backward multiplies by the BF16 weights `wh` the forward used
     const MlpOffsets O;
     float *a1 = work, *h1 = a1 + (int64_t)P * MLP_H, *a2 = h1 + (int64_t)P * MLP_H, *h2 = a2 + (int64_t)P * MLP_H;
     float *y = h2 + (int64_t)P * MLP_H, *dy = y + (int64_t)P * MLP_OUT;
