@@ -58,15 +58,16 @@ __device__ __forceinline__ void colsum_vec(const void *base, const RowChunk &ch,
     }
 }
 
-__global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks, int d,
-                                 int dtype, i128 *__restrict__ part, int *__restrict__ bad)
+__global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks, int c0,
+                                 int d, int dtype, i128 *__restrict__ part, int *__restrict__ bad)
 {
-    const RowChunk ch = chunks[blockIdx.x];
+    const int ci = c0 + (int)blockIdx.x;  // chunk index
+    const RowChunk ch = chunks[ci];
     const PairMeta pm = meta[ch.pair];
     const void *base = ch.side ? pm.Y : pm.X;
     const int esz = dtype == DT_F32 ? 4 : 2;
     bool ok = true;
-    i128 *out = part + (int64_t)blockIdx.x * d;
+    i128 *out = part + (int64_t)ci * d;
     if ((d * esz) % 16 == 0 && ((uintptr_t)base & 15u) == 0) {
         if (dtype == DT_F32) colsum_vec<DT_F32>(base, ch, d, out, ok);
         else colsum_vec<DT_BF16>(base, ch, d, out, ok);
@@ -85,12 +86,12 @@ __global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChu
     if (!ok) atomicOr(bad + ch.pair, 1);
 }
 
-// s[(p*2 + side)*d + j] = sum over the chunks of (p, side)
-__global__ void k_colsum_reduce(const PairMeta *__restrict__ meta, int P, int d, const i128 *__restrict__ part,
-                                i128 *__restrict__ s)
+// s[(p*2 + side)*d + j] = sum over the chunks of (p, side), pairs p0 .. p1-1
+__global__ void k_colsum_reduce(const PairMeta *__restrict__ meta, int p0, int p1, int d,
+                                const i128 *__restrict__ part, i128 *__restrict__ s)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)P * 2 * d) return;
+    const int64_t idx = (int64_t)p0 * 2 * d + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)p1 * 2 * d) return;
     const int j = (int)(idx % d);
     const int ps = (int)(idx / d);
     const int p = ps >> 1, side = ps & 1;
@@ -103,13 +104,13 @@ __global__ void k_colsum_reduce(const PairMeta *__restrict__ meta, int P, int d,
 }
 
 // ---------------------------------------------------------------------------
-// Axis: one block of 64 threads per pair; dynamic smem 2*d doubles.
+// Axis: one block of 64 threads per pair (p0 + block); dynamic smem 2*d doubles.
 // ---------------------------------------------------------------------------
-__global__ void k_axis(const PairMeta *__restrict__ meta, const RunOpts o, const i128 *__restrict__ s,
+__global__ void k_axis(const PairMeta *__restrict__ meta, int p0, const RunOpts o, const i128 *__restrict__ s,
                        const int *__restrict__ bad, PairState *__restrict__ st, double *__restrict__ u)
 {
     extern __shared__ double sm_axis[];
-    const int p = blockIdx.x;
+    const int p = p0 + (int)blockIdx.x;
     const PairMeta pm = meta[p];
     const int d = o.d;
     double *xb = sm_axis, *yb = sm_axis + d;
@@ -192,7 +193,7 @@ __device__ __noinline__ double reflect_chain(const void *src, int64_t row, int d
 
 template <int DT>
 __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
-                                                 const RunOpts o, const PairState *__restrict__ st,
+                                                 int c0, const RunOpts o, const PairState *__restrict__ st,
                                                  const double *__restrict__ u, void *__restrict__ Z,
                                                  unsigned int *__restrict__ colmax)
 {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
     __shared__ double cs[CHUNK_ROWS];      // FP32 storage: -2c per row; BF16: -2c of fallback rows
     __shared__ float ah_s[CHUNK_ROWS], al_s[CHUNK_ROWS], dl_s[CHUNK_ROWS];
     __shared__ int chain_s[CHUNK_ROWS];    // BF16: cs[r] holds the exact -2c
-    const RowChunk ch = chunks[blockIdx.x];
+    const RowChunk ch = chunks[c0 + (int)blockIdx.x];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
     const int d = o.d;
@@ -429,7 +430,8 @@ constexpr int ZS_ROWS = CHUNK_ROWS / ZS_PARTS;     // 16
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restrict__ meta,
-                                                        const RowChunk *__restrict__ chunks, const RunOpts o,
+                                                        const RowChunk *__restrict__ chunks, int c0,
+                                                        const RunOpts o,
                                                         const PairState *__restrict__ st, const void *__restrict__ Z,
                                                         const unsigned int *__restrict__ colmax,
                                                         i128 *__restrict__ tpart, float *__restrict__ cpart,
@@ -438,7 +440,8 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
     __shared__ unsigned short sq[3][ZS_T][CHUNK_ROWS + 2];
     __shared__ i128 acc_s[ZS_PARTS][ZS_T];
     __shared__ float cacc_s[ZS_PARTS][ZS_T];
-    const RowChunk ch = chunks[blockIdx.x];
+    const int ci = c0 + (int)blockIdx.x;  // chunk index
+    const RowChunk ch = chunks[ci];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
     const int d = o.d;
@@ -502,8 +505,8 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
                 a += acc_s[q][threadIdx.x];
                 c = __fadd_ru(c, cacc_s[q][threadIdx.x]);
             }
-            tpart[(int64_t)blockIdx.x * d + j0 + threadIdx.x] = a;
-            cpart[(int64_t)blockIdx.x * d + j0 + threadIdx.x] = c;
+            tpart[(int64_t)ci * d + j0 + threadIdx.x] = a;
+            cpart[(int64_t)ci * d + j0 + threadIdx.x] = c;
         }
         __syncthreads();
     }
@@ -590,13 +593,14 @@ __device__ __noinline__ SlowCol zs_slow_column(uint32_t w0, uint32_t w1, uint32_
 }
 
 __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restrict__ meta,
-                                                    const RowChunk *__restrict__ chunks, const RunOpts o,
+                                                    const RowChunk *__restrict__ chunks, int c0, const RunOpts o,
                                                     const PairState *__restrict__ st, const uint4 *__restrict__ Z,
                                                     const unsigned int *__restrict__ colmax,
                                                     i128 *__restrict__ tpart, float *__restrict__ cpart,
                                                     unsigned short *__restrict__ zq, int64_t zq_ld)
 {
-    const RowChunk ch = chunks[blockIdx.x];
+    const int ci = c0 + (int)blockIdx.x;  // chunk index
+    const RowChunk ch = chunks[ci];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
     const int d = o.d, cw = o.cw;
@@ -707,8 +711,8 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
         if (ln < 8) {
             i128 tot = my_slow;
             if (my_fast) tot += ((i128)my_ih << (my_E + 79)) + ((i128)my_il << (my_E + 70));
-            tpart[(int64_t)blockIdx.x * d + j + ln] = tot;
-            cpart[(int64_t)blockIdx.x * d + j + ln] = my_ca;
+            tpart[(int64_t)ci * d + j + ln] = tot;
+            cpart[(int64_t)ci * d + j + ln] = my_ca;
         }
         // the last chunk of the pair also zero-fills the padded tokens of the slices
         for (int k = ln; k < 16 * npad; k += 32) {
@@ -718,15 +722,16 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
     }
 }
 
-// Per (pair, column): exact totals, observed group-1 sums, band constants.
-__global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int P, const RunOpts o,
+// Per (pair, column) of pairs p0 .. p1-1: exact totals, observed group-1 sums,
+// band constants.
+__global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p1, const RunOpts o,
                                 const PairState *__restrict__ st, const unsigned int *__restrict__ colmax,
                                 const i128 *__restrict__ tpart, const float *__restrict__ cpart,
                                 i128 *__restrict__ t_ex, i128 *__restrict__ s1o, ColConst *__restrict__ cc)
 {
     const int d = o.d;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)P * o.d_pad) return;
+    const int64_t idx = (int64_t)p0 * o.d_pad + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)p1 * o.d_pad) return;
     const int p = (int)(idx / o.d_pad), j = (int)(idx % o.d_pad);
     const PairMeta pm = meta[p];
     ColConst c{0.0f, 0.0f, 0.0f, 0.0f};
@@ -763,13 +768,14 @@ __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int P, const 
 }
 
 // ---------------------------------------------------------------------------
-// Observed statistic, one block of 64 threads per pair; dynamic smem 2*d doubles.
+// Observed statistic, one block of 64 threads per pair (p0 + block); dynamic
+// smem 2*d doubles.
 // ---------------------------------------------------------------------------
-__global__ void k_tobs(const PairMeta *__restrict__ meta, const RunOpts o, const i128 *__restrict__ t_ex,
+__global__ void k_tobs(const PairMeta *__restrict__ meta, int p0, const RunOpts o, const i128 *__restrict__ t_ex,
                        const i128 *__restrict__ s1o, const ColConst *__restrict__ cc, PairState *__restrict__ st)
 {
     extern __shared__ double sm_tobs[];
-    const int p = blockIdx.x;
+    const int p = p0 + (int)blockIdx.x;
     if (st[p].status != ST_OK) return;
     const PairMeta pm = meta[p];
     const int d = o.d;
@@ -823,49 +829,56 @@ __global__ void k_tobs(const PairMeta *__restrict__ meta, const RunOpts o, const
 // ---------------------------------------------------------------------------
 static inline unsigned cdiv_(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-void launch_colsum(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, int d, int dtype, i128 *part,
+void launch_colsum(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, int d, int dtype, i128 *part,
                    i128 *s, int *bad, cudaStream_t st)
 {
+    if (sp.c1 <= sp.c0 || sp.p1 <= sp.p0) return;
     // one thread per 16-byte column group when rows can be 16-byte aligned, else per column
     const int esz = dtype == DT_F32 ? 4 : 2, groups = (d * esz) % 16 == 0 ? d * esz / 16 : d;
     const int threads = std::min(256, std::max(32, (groups + 31) / 32 * 32));
-    k_colsum_partial<<<nch, threads, 0, st>>>(meta, chunks, d, dtype, part, bad);
-    k_colsum_reduce<<<cdiv_((int64_t)P * 2 * d, 256), 256, 0, st>>>(meta, P, d, part, s);
+    k_colsum_partial<<<sp.c1 - sp.c0, threads, 0, st>>>(meta, chunks, sp.c0, d, dtype, part, bad);
+    k_colsum_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * 2 * d, 256), 256, 0, st>>>(meta, sp.p0, sp.p1, d, part, s);
 }
 
-void launch_axis(const PairMeta *meta, int P, const RunOpts &o, const i128 *s, const int *bad, PairState *pst,
-                 double *u, cudaStream_t st)
+void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *s, const int *bad,
+                 PairState *pst, double *u, cudaStream_t st)
 {
-    k_axis<<<P, 64, 2 * sizeof(double) * o.d, st>>>(meta, o, s, bad, pst, u);
+    if (sp.p1 <= sp.p0) return;
+    k_axis<<<sp.p1 - sp.p0, 64, 2 * sizeof(double) * o.d, st>>>(meta, sp.p0, o, s, bad, pst, u);
 }
 
-void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, const RunOpts &o,
+void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                     const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st)
 {
-    if (o.dtype == DT_F32) k_reflect<DT_F32><<<nch, 128, 0, st>>>(meta, chunks, o, pst, u, Z, colmax);
-    else k_reflect<DT_BF16><<<nch, 128, 0, st>>>(meta, chunks, o, pst, u, Z, colmax);
+    if (sp.c1 <= sp.c0) return;
+    const unsigned nc = (unsigned)(sp.c1 - sp.c0);
+    if (o.dtype == DT_F32) k_reflect<DT_F32><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax);
+    else k_reflect<DT_BF16><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax);
 }
 
-void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
+void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
                    unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
                    cudaStream_t st)
 {
+    if (sp.c1 <= sp.c0 || sp.p1 <= sp.p0) return;
+    const unsigned nc = (unsigned)(sp.c1 - sp.c0);
     if (o.dtype == DT_F32)
-        k_zstats_partial<DT_F32><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+        k_zstats_partial<DT_F32><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
     else if (tok_layout)
-        k_zstats_tok<<<nch, 256, 0, st>>>(meta, chunks, o, pst, static_cast<const uint4 *>(Z), colmax, tpart, cpart,
-                                          zq, zq_ld);
+        k_zstats_tok<<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, static_cast<const uint4 *>(Z), colmax, tpart,
+                                         cpart, zq, zq_ld);
     else
-        k_zstats_partial<DT_BF16><<<nch, 256, 0, st>>>(meta, chunks, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
-    k_zstats_reduce<<<cdiv_((int64_t)P * o.d_pad, 256), 256, 0, st>>>(meta, P, o, pst, colmax, tpart, cpart, t_ex,
-                                                                        s1o, cc);
+        k_zstats_partial<DT_BF16><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+    k_zstats_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * o.d_pad, 256), 256, 0, st>>>(meta, sp.p0, sp.p1, o, pst, colmax,
+                                                                                   tpart, cpart, t_ex, s1o, cc);
 }
 
-void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
+void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
                  const ColConst *cc, PairState *pst, cudaStream_t st)
 {
-    k_tobs<<<P, 64, 2 * sizeof(double) * o.d, st>>>(meta, o, t_ex, s1o, cc, pst);
+    if (sp.p1 <= sp.p0) return;
+    k_tobs<<<sp.p1 - sp.p0, 64, 2 * sizeof(double) * o.d, st>>>(meta, sp.p0, o, t_ex, s1o, cc, pst);
 }
 
 void set_align_attributes()

@@ -5,7 +5,8 @@
 //          -> exact recheck -> finalize -> one device-to-host copy
 //
 // Everything between the metadata upload and the result download runs on the
-// caller's stream with no host round trip.
+// caller's stream with no host round trip.  Host input is copied in pieces of
+// whole pairs, and colsum .. tobs run per piece as the pieces arrive.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -55,6 +56,7 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int LABEL_CHUNKS = 4;  // label-draw chunks of a mixed-path call
+constexpr int ALIGN_PIECES = 8;  // pieces of the host-to-device input copy, aligned as they arrive
 }
 
 struct hb_ctx {
@@ -80,6 +82,10 @@ struct hb_ctx {
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, enter = nullptr, leave = nullptr;
     cudaEvent_t lab_ev[LABEL_CHUNKS] = {};  // label chunk c drawn
+    // host input: the copy runs on `copy`, piece by piece, beside the
+    // alignment of the pieces already copied
+    cudaStream_t copy = nullptr;
+    cudaEvent_t cp_ev[ALIGN_PIECES] = {};  // input piece k copied
     // route table of HB_PATH_AUTO, per size bucket (hb_autotune)
     int32_t route[HB_ROUTE_BUCKETS];
     bool tuned = false;
@@ -121,8 +127,9 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
         cudaEventCreateWithFlags(&c->enter, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->leave, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->main, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
-        !create_events(c->lab_ev, LABEL_CHUNKS) ||
-        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess) {
+        !create_events(c->lab_ev, LABEL_CHUNKS) || !create_events(c->cp_ev, ALIGN_PIECES) ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) != cudaSuccess) {
         hb_ctx_destroy(c);
         return fail(HB_ERR_CUDA, "stream or event creation failed");
     }
@@ -143,7 +150,7 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
         if (c->tev[k]) cudaEventDestroy(c->tev[k]);
     for (cudaEvent_t e : c->gev)
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t q : {c->main, c->side})
+    for (cudaStream_t q : {c->main, c->side, c->copy})
         if (q) {
             cudaStreamSynchronize(q);
             cudaStreamDestroy(q);
@@ -151,6 +158,8 @@ extern "C" void hb_ctx_destroy(hb_ctx *c)
     for (cudaEvent_t e : {c->fork, c->join, c->enter, c->leave})
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->lab_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->cp_ev)
         if (e) cudaEventDestroy(e);
     if (c->tbuf) cudaFree(c->tbuf);
     if (c->ws) cudaFree(c->ws);
@@ -510,6 +519,8 @@ struct Exec {
     bool capture = false;    // enqueued under stream capture (events become graph nodes)
     cudaEvent_t *lab_ev = nullptr;  // LABEL_CHUNKS events: label chunk c drawn (mixed path)
     cudaEvent_t *gev = nullptr;     // 2 * LABEL_CHUNKS timing events around the GEMM launches, or nullptr
+    cudaStream_t copy = nullptr;    // host input: stream of the piecewise input copy (else one copy on s)
+    cudaEvent_t *cp_ev = nullptr;   // ALIGN_PIECES events: input piece k copied
 };
 
 static void xrec(const Exec &ex, cudaEvent_t e)
@@ -530,10 +541,35 @@ static float gemm_ms(const Plan &pl, const cudaEvent_t *gev)
     return total;
 }
 
-// Kernel launches of one test call: colsum (2) + axis + reflect + zstats (2) +
-// tobs + label draws + GEMM + recheck (2 per batch) + finalize.
-static int launch_count(const Plan &pl, unsigned int cap, int rgrid)
+// Cuts the pairs into at most `pieces` ranges of whole pairs with about equal
+// input rows (every range holds at least one pair); returns the number of
+// ranges.
+static int piece_spans(const Plan &pl, int pieces, PairSpan *sp)
 {
+    const int P = pl.P, nch = (int)pl.chunks.size();
+    int64_t total = 0;
+    for (int p = 0; p < P; ++p) total += pl.meta[p].N;
+    int n = 0, p = 0;
+    int64_t acc = 0;
+    for (int k = 0; k < pieces && p < P; ++k) {
+        const int64_t target = total * (k + 1) / pieces;
+        const int p0 = p;
+        do {
+            acc += pl.meta[p].N;
+            ++p;
+        } while (p < P && acc < target);
+        sp[n++] = PairSpan{p0, p, pl.meta[p0].chunk0, p < P ? pl.meta[p].chunk0 : nch};
+    }
+    return n;
+}
+
+// Kernel launches of one test call: colsum (2) + axis + reflect + zstats (2) +
+// tobs (per input piece when the input comes from the host) + label draws +
+// GEMM + recheck (2 per batch) + finalize.
+static int launch_count(const Plan &pl, unsigned int cap, int rgrid, bool host_input)
+{
+    PairSpan sp[ALIGN_PIECES];
+    const int pieces = host_input ? piece_spans(pl, ALIGN_PIECES, sp) : 1;
     const bool mixed = pl.o.path == HB_PATH_MIXED;
     const int pchunks = (pl.P + 65534) / 65535;
     int labels = pchunks, gemm = pchunks;
@@ -543,7 +579,7 @@ static int launch_count(const Plan &pl, unsigned int cap, int rgrid)
         gemm = 0;
         for (int c = 0; c < pl.nlc; ++c) gemm += pl.lc_item[c + 1] > pl.lc_item[c] ? 1 : 0;
     }
-    return 8 + labels + gemm + 2 * (int)((cap + rgrid - 1) / rgrid);
+    return 7 * pieces + 1 + labels + gemm + 2 * (int)((cap + rgrid - 1) / rgrid);
 }
 
 static void xmark(const Exec &ex, int k)
@@ -567,10 +603,10 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     const int d = o.d;
     const bool mixed = o.path == HB_PATH_MIXED;
     const bool chunked = mixed && !features && pl.nlc > 0;
+    CK(cudaEventRecord(ex.fork, s));
     if (!features) {
         // labels on the side stream from here on, concurrently with steps 1-4 and,
         // chunk by chunk, with the GEMM of the chunks drawn before
-        CK(cudaEventRecord(ex.fork, s));
         CK(cudaStreamWaitEvent(ex.side, ex.fork, 0));
         if (chunked) {
             for (int c = 0; c < pl.nlc; ++c) {
@@ -583,30 +619,52 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         }
         CK(cudaEventRecord(ex.join, ex.side));
     }
-    if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
     CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
     if (mixed && o.d_pad != d)
         CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
 
-    const unsigned int nch = (unsigned int)pl.chunks.size();
-    // steps 1-3 (column maxima feed the slice scales and the exact-sum windows)
-    xmark(ex, 0);
-    launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
-    launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
-    launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, b.colmax, s);
-    CK(cudaGetLastError());
-
-    // step 4: Z statistics, fixed-point slices, T_obs
-    const int64_t zq_ld = pl.total_rows_pad;
-    xmark(ex, 1);
+    // Host input is copied in pieces of whole pairs on the copy stream, and
+    // steps 1-4 of the pairs of piece k run as soon as its bytes are in, beside
+    // the copy of the pieces after it.  Every step before the GEMM works pair
+    // by pair, so the pieces give the same results as one pass over all pairs.
+    PairSpan spans[ALIGN_PIECES];
+    int pieces = 1;
+    spans[0] = PairSpan{0, P, 0, (int)pl.chunks.size()};
+    if (xy_host && ex.copy) {
+        pieces = piece_spans(pl, ALIGN_PIECES, spans);
+        CK(cudaStreamWaitEvent(ex.copy, ex.fork, 0));
+        for (int k = 0; k < pieces; ++k) {
+            const size_t lo = (size_t)((const char *)pl.meta[spans[k].p0].X - (const char *)b.xy);
+            const size_t hi = spans[k].p1 < P ? (size_t)((const char *)pl.meta[spans[k].p1].X - (const char *)b.xy)
+                                              : xy_bytes;
+            CK(cudaMemcpyAsync((char *)b.xy + lo, (const char *)xy_host + lo, hi - lo, cudaMemcpyHostToDevice,
+                               ex.copy));
+            CK(cudaEventRecord(ex.cp_ev[k], ex.copy));
+        }
+    } else if (xy_host) {
+        CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
+    }
     // lanes-along-tokens slices: tensor-core path, two BF16 slices, 16-byte rows
     const bool tok_layout = mixed && o.slices == 2 && d % 8 == 0;
-    launch_zstats(b.meta, b.chunks, nch, P, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o, b.cc,
-                  tok_layout,
-                  s);
-    launch_tobs(b.meta, P, o, b.t_ex, b.s1o, b.cc, b.st, s);
-    CK(cudaGetLastError());
+    const int64_t zq_ld = pl.total_rows_pad;
+    xmark(ex, 0);
+    for (int k = 0; k < pieces; ++k) {
+        const PairSpan &sp = spans[k];
+        if (pieces > 1) CK(cudaStreamWaitEvent(s, ex.cp_ev[k], 0));
+        // steps 1-3 (column maxima feed the slice scales and the exact-sum windows)
+        launch_colsum(b.meta, b.chunks, sp, d, o.dtype, b.part, b.s, b.bad, s);
+        launch_axis(b.meta, sp, o, b.s, b.bad, b.st, b.u, s);
+        launch_reflect(b.meta, b.chunks, sp, o, b.st, b.u, Z, b.colmax, s);
+        CK(cudaGetLastError());
+        // step 4: Z statistics, fixed-point slices, T_obs
+        if (pieces == 1) xmark(ex, 1);
+        launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o, b.cc,
+                      tok_layout, s);
+        launch_tobs(b.meta, sp, o, b.t_ex, b.s1o, b.cc, b.st, s);
+        CK(cudaGetLastError());
+    }
+    if (pieces > 1) xmark(ex, 1);  // piecewise: the "align" stage holds steps 1-4 and the copy
 
     if (features) {
         xmark(ex, 2);
@@ -738,11 +796,11 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         CK(cudaEventRecord(c->stage_done, s));
         if (align_only) {
             if (xy_host) CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
-            const unsigned int nch = (unsigned int)pl.chunks.size();
+            const PairSpan all{0, P, 0, (int)pl.chunks.size()};
             mark(c, 0, s);
-            launch_colsum(b.meta, b.chunks, nch, P, d, o.dtype, b.part, b.s, b.bad, s);
-            launch_axis(b.meta, P, o, b.s, b.bad, b.st, b.u, s);
-            launch_reflect(b.meta, b.chunks, nch, o, b.st, b.u, Z, nullptr, s);
+            launch_colsum(b.meta, b.chunks, all, d, o.dtype, b.part, b.s, b.bad, s);
+            launch_axis(b.meta, all, o, b.s, b.bad, b.st, b.u, s);
+            launch_reflect(b.meta, b.chunks, all, o, b.st, b.u, Z, nullptr, s);
             CK(cudaGetLastError());
             if (u_out) CK(cudaMemcpyAsync(u_out, b.u, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
             if (skipped_out) {
@@ -759,6 +817,8 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         Exec ex{s, c->side, c->fork, c->join, c->timing ? c->tev : nullptr, c->sms};
         ex.lab_ev = c->lab_ev;
         ex.gev = c->timing && !tri ? c->gev : nullptr;
+        ex.copy = c->copy;
+        ex.cp_ev = c->cp_ev;
         hs = enqueue_test(ex, pl, b, Z, xy_host, xy_bytes, T_out, tri, cap, rgrid, c->stage);
         if (hs != HB_OK) return hs;
         char *h = (char *)c->stage;
@@ -775,7 +835,7 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&c->last_ms[k], c->tev[k], c->tev[k + 1]);
             c->last_ms[6] = tri ? 0.f : gemm_ms(pl, c->gev);
         }
-        c->last_launches = launch_count(pl, cap, rgrid);
+        c->last_launches = launch_count(pl, cap, rgrid, xy_host != nullptr);
         return HB_OK;
     }
     return fail(HB_ERR_CUDA, "recheck list kept overflowing");
@@ -1129,7 +1189,7 @@ static hb_status plan_build(hb_plan *q, int64_t P)
     if (ce != cudaSuccess || !g) return fail(HB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
     q->graph = g;
     CK(cudaGraphInstantiateWithFlags(&q->exec, g, cudaGraphInstantiateFlagUseNodePriority));
-    q->launches = launch_count(pl, q->cap, q->rgrid);
+    q->launches = launch_count(pl, q->cap, q->rgrid, false);
     return HB_OK;
 }
 

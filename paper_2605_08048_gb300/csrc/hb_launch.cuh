@@ -9,17 +9,25 @@
 #include "hb_internal.cuh"
 
 namespace hb {
-void launch_colsum(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, int d, int dtype, i128 *part,
+// A contiguous range of pairs, p0 .. p1-1, and of their row chunks, c0 .. c1-1
+// (the chunks of a pair follow one another, pair by pair).  The alignment and
+// Z-statistics launchers work on one range, so a call can align the pairs
+// whose input has arrived while the rest is still being copied.
+struct PairSpan {
+    int p0, p1;
+    int c0, c1;
+};
+void launch_colsum(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, int d, int dtype, i128 *part,
                    i128 *s, int *bad, cudaStream_t st);
-void launch_axis(const PairMeta *meta, int P, const RunOpts &o, const i128 *s, const int *bad, PairState *pst,
-                 double *u, cudaStream_t st);
-void launch_reflect(const PairMeta *meta, const RowChunk *chunks, unsigned nch, const RunOpts &o,
+void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *s, const int *bad,
+                 PairState *pst, double *u, cudaStream_t st);
+void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                     const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st);
-void launch_zstats(const PairMeta *meta, const RowChunk *chunks, unsigned nch, int P, const RunOpts &o,
+void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
                    unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
                    cudaStream_t st);
-void launch_tobs(const PairMeta *meta, int P, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
+void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
                  const ColConst *cc, PairState *pst, cudaStream_t st);
 void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
                         cudaStream_t st);

@@ -153,9 +153,10 @@ extern "C" hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, i
     double *u = (double *)(base + L.u);
 
     k_noalloc_setup<<<(nch + 127) / 128, 128, 0, s>>>(pm, nch_x, nch_y, L.meta, L.chunks, L.bad);
-    launch_colsum(meta, chunks, (unsigned)nch, 1, (int)d, dtype, part, sums, bad, s);
-    launch_axis(meta, 1, o, sums, bad, st, u, s);
-    launch_reflect(meta, chunks, (unsigned)nch, o, st, u, Z_out, nullptr, s);
+    const PairSpan all{0, 1, 0, nch};
+    launch_colsum(meta, chunks, all, (int)d, dtype, part, sums, bad, s);
+    launch_axis(meta, all, o, sums, bad, st, u, s);
+    launch_reflect(meta, chunks, all, o, st, u, Z_out, nullptr, s);
     if (cudaGetLastError() != cudaSuccess) return HB_ERR_CUDA;
     if (u_out && cudaMemcpyAsync(u_out, u, sizeof(double) * (size_t)d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return HB_ERR_CUDA;

@@ -230,6 +230,35 @@ def test_batched_host_input_equals_device_input(ctx, path):
     assert a == c
 
 
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_host_input_pieces_parity(ctx, path):
+    """Host input is copied in pieces of whole pairs, each piece aligned as it
+    arrives: with more pairs than pieces, ragged sizes, a pair holding a NaN and
+    a pair with n = 1, every pair's result equals the oracle's and the
+    device-input call's."""
+    rng = np.random.default_rng(29)
+    P = 21
+    n, m = rng.integers(2, 160, P), rng.integers(2, 160, P)
+    n[4] = 1
+    b = synth.batch(29, P, d=64, dtype="bf16", sizes=(n, m))
+    XY = b.XY.copy()
+    XY[b.offsets[9] + 3, 5] = 0x7FC0  # a BF16 NaN in pair 9
+    o = H.make_opts(B=200, seed=3, path=path)
+    refs = O.perm_test_batched(XY, b.n, b.m, O.opts(B=200, seed=3))
+    hx = torch.from_numpy(XY.view(np.int16)).view(torch.bfloat16).pin_memory()
+    res = H.hb_perm_test_batched(ctx, hx, b.n, b.m, o, check=False)
+    on_dev = H.hb_perm_test_batched(ctx, dev(XY), b.n, b.m, o, check=False)
+    assert np.array_equal(res.column("status"), on_dev.column("status"))
+    assert res[4]["status"] != 0 and res[9]["status"] != 0
+    valid = [p for p in range(P) if res[p]["status"] == 0]
+    assert [res[p] for p in valid] == [on_dev[p] for p in valid]
+    for r, ref in zip(res, refs):
+        assert r["status"] == ref["status"]
+        if ref["status"] == 0:
+            assert r["count"] == ref["count"] and r["p"] == ref["p"]
+            assert r["r_x"] == ref["r_x"] and r["r_y"] == ref["r_y"]
+
+
 def test_status_codes(ctx):
     X, Y = synth.pair(1, 10, 12, 16, 0.35, 0.35, None, "f32")
     Xn = X.copy()
