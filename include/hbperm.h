@@ -14,7 +14,9 @@
  *  - Data pointers (X, Y, Z, label bits, T_out) are DEVICE pointers owned by
  *    the caller, except where an argument says "host".  The library never
  *    frees caller memory.  hb_perm_test_batched also accepts host memory for
- *    XY (it then stages the copy itself).
+ *    XY (pinned memory copies fastest): it then copies XY itself, in pieces
+ *    of whole pairs whose alignment starts as each piece arrives, and reads
+ *    the host buffer only until the call returns.
  *  - Matrices are row-major, one embedding per row, rows contiguous.
  *    dtype HB_F32 = IEEE binary32, HB_BF16 = bfloat16 (16-bit patterns).
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
