@@ -820,7 +820,15 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
         ex.copy = c->copy;
         ex.cp_ev = c->cp_ev;
         hs = enqueue_test(ex, pl, b, Z, xy_host, xy_bytes, T_out, tri, cap, rgrid, c->stage);
-        if (hs != HB_OK) return hs;
+        if (hs != HB_OK) {
+            // a failed enqueue may leave the label draws or the input copy running
+            // on their own streams: let them end before the caller reuses the input
+            // buffer or the context reuses the workspace
+            cudaStreamSynchronize(c->side);
+            cudaStreamSynchronize(c->copy);
+            cudaGetLastError();
+            return hs;
+        }
         char *h = (char *)c->stage;
         CK(cudaStreamSynchronize(s));
         const unsigned int *cnt = (const unsigned int *)h;
