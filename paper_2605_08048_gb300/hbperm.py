@@ -111,6 +111,27 @@ def _sizes(v) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(v, dtype=np.int64))
 
 
+def _packed(XY: torch.Tensor, na: np.ndarray, ma: np.ndarray) -> None:
+    """The library reads sum(n + m) rows of d values from the XY pointer it is
+    given, so the tensor must hold exactly that many rows, contiguously, and n
+    and m must give one size per pair."""
+    if XY.dim() != 2 or not XY.is_contiguous():
+        raise ValueError("XY must be a contiguous 2-D tensor")
+    if na.ndim != 1 or na.shape != ma.shape:
+        raise ValueError("n and m must be 1-D with one entry per pair")
+    rows = int(na.sum()) + int(ma.sum())
+    if rows != XY.shape[0]:
+        raise ValueError(f"XY has {XY.shape[0]} rows but the pair sizes add up to {rows}")
+
+
+def _pair(X: torch.Tensor, Y: torch.Tensor) -> None:
+    """X and Y of one pair: 2-D, one dtype, one embedding dimension."""
+    if X.dim() != 2 or Y.dim() != 2:
+        raise ValueError("X and Y must be 2-D (rows = embeddings)")
+    if X.dtype != Y.dtype or X.shape[1] != Y.shape[1]:
+        raise ValueError("X and Y must have the same dtype and embedding dimension")
+
+
 def _results(P: int):
     arr = np.zeros(P, dtype=RESULT_DTYPE)
     return arr, arr.ctypes.data_as(C.POINTER(hb_result))
@@ -214,8 +235,8 @@ class Context:
 
 def hb_align(ctx: Context, X: torch.Tensor, Y: torch.Tensor, align=1, reflect_side=0, stream=None):
     """Returns (Z [n+m][d] same dtype, u [d] float64, skipped)."""
+    _pair(X, Y)
     dt = _dtype_code(X)
-    assert Y.dtype == X.dtype and X.shape[1] == Y.shape[1]
     n, d = X.shape
     m = Y.shape[0]
     Z = torch.empty((n + m, d), dtype=X.dtype, device=X.device)
@@ -232,6 +253,7 @@ def hb_align_noalloc(X: torch.Tensor, Y: torch.Tensor, align=1, reflect_side=0, 
     instead of a context workspace.  The caller provides the output buffers;
     here they are allocated by torch only because this is a Python test
     harness.  Returns (Z, u, skipped)."""
+    _pair(X, Y)
     L = lib()
     L.hb_align_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
@@ -250,6 +272,7 @@ def hb_align_noalloc(X: torch.Tensor, Y: torch.Tensor, align=1, reflect_side=0, 
 def hb_perm_test(ctx: Context, X: torch.Tensor, Y: torch.Tensor, opts: hb_opts, want_T=False, stream=None,
                  check=True):
     """Returns (result dict, T_b float32 tensor or None)."""
+    _pair(X, Y)
     dt = _dtype_code(X)
     n, d = X.shape
     m = Y.shape[0]
@@ -272,10 +295,9 @@ def hb_perm_test_batched(ctx: Context, XY: torch.Tensor, n, m, opts: hb_opts, st
     """XY packs, per pair, n[p] rows of X then m[p] rows of Y (device or host
     tensor).  Returns a Results sequence: one result dict per pair."""
     dt = _dtype_code(XY)
-    d = XY.shape[1]
-    if not XY.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
     na, ma = _sizes(n), _sizes(m)
+    _packed(XY, na, ma)
+    d = XY.shape[1]
     P = len(na)
     arr, res = _results(P)
     st = lib().hb_perm_test_batched(ctx.handle, P, C.c_void_p(XY.data_ptr()), na.ctypes.data, ma.ctypes.data, d, dt,
@@ -294,16 +316,19 @@ class Plan:
         self.d = int(d)
         self.dtype = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
         na, ma = _sizes(n), _sizes(m)
+        if na.ndim != 1 or na.shape != ma.shape:
+            raise ValueError("n and m must be 1-D with one entry per pair")
+        self.rows = int(na.sum()) + int(ma.sum())
         h = C.c_void_p()
         _check(lib().hb_plan_create(ctx.handle, self.P, na.ctypes.data, ma.ctypes.data, self.d, self.dtype, C.byref(opts), C.byref(h)))
         self._h = h
         self._ctx = ctx  # the plan keeps the context alive
 
     def execute(self, XY: torch.Tensor, stream=None, check=True):
-        if not XY.is_contiguous():
-            raise ValueError("expected a contiguous tensor")
-        if XY.shape[1] != self.d or _dtype_code(XY) != self.dtype:
-            raise ValueError("XY does not match the plan's d / dtype")
+        if XY.dim() != 2 or not XY.is_contiguous():
+            raise ValueError("XY must be a contiguous 2-D tensor")
+        if XY.shape != (self.rows, self.d) or _dtype_code(XY) != self.dtype:
+            raise ValueError("XY does not match the plan's rows / d / dtype")
         arr, res = _results(self.P)
         st = lib().hb_plan_execute(self._h, C.c_void_p(XY.data_ptr()), res, _stream(stream))
         if check:
@@ -392,6 +417,7 @@ class hb_mlp(C.Structure):
 
 def _batched_args(XY, n, m):
     na, ma = _sizes(n), _sizes(m)
+    _packed(XY, na, ma)
     return len(na), (C.c_int64 * len(na)).from_buffer(na), (C.c_int64 * len(ma)).from_buffer(ma)
 
 

@@ -78,3 +78,28 @@ def test_results_array_mirrors_hb_result():
     other = arr.copy()
     other["count"][2] += 1
     assert res != H.Results(other)
+
+
+def test_binding_checks_shapes_before_calling_the_library():
+    """The library reads sum(n + m) rows from the pointer it is given, so the
+    binding rejects a packed tensor of another row count, size lists of
+    different lengths, and pairs whose X and Y differ in dtype or dimension,
+    before any call (no context or GPU is needed to see the error)."""
+    torch = pytest.importorskip("torch")
+    o = H.make_opts(B=99)
+    XY = torch.zeros((30, 16), dtype=torch.bfloat16)
+    with pytest.raises(ValueError, match="rows"):
+        H.hb_perm_test_batched(None, XY, [10, 5], [10, 4], o)
+    with pytest.raises(ValueError, match="one entry per pair"):
+        H.hb_perm_test_batched(None, XY, [10, 5], [15], o)
+    with pytest.raises(ValueError, match="2-D"):
+        H.hb_perm_test_batched(None, XY.reshape(-1), [10, 5], [10, 5], o)
+    with pytest.raises(ValueError, match="contiguous"):
+        H.hb_perm_test_batched(None, torch.zeros((16, 30), dtype=torch.bfloat16).t(), [10, 5], [10, 5], o)
+    X, Y = torch.zeros((4, 16)), torch.zeros((5, 8))
+    for call in (lambda: H.hb_perm_test(None, X, Y, o), lambda: H.hb_align(None, X, Y),
+                 lambda: H.hb_align_noalloc(X, Y)):
+        with pytest.raises(ValueError, match="dimension"):
+            call()
+    with pytest.raises(ValueError, match="dtype"):
+        H.hb_perm_test(None, X, torch.zeros((5, 16), dtype=torch.bfloat16), o)
