@@ -181,6 +181,33 @@ hb_status hb_plan_execute(hb_plan *plan, const void *XY, hb_result *out, void *s
 /* Frees the plan's graph, streams, workspace and staging (NULL is a no-op). */
 void hb_plan_destroy(hb_plan *plan);
 
+/* The launch layout hb_perm_test_batched would use for sizes n, m (host, P
+ * entries), d, dtype and opts (opts->path must not be HB_PATH_AUTO, whose
+ * routes live in a context).  Host computation only: no context, no GPU and
+ * no CUDA call, so it serves diagnostics and host-side tests.  counts (host)
+ * receives the four sizes below; each array (host, nullable, int32) receives
+ * its rows when not NULL, so a first call with NULL arrays sizes them:
+ *   chunks       [n_chunks][4]   pair, side (0 = X, 1 = Y), first row, rows:
+ *                the row chunks of the alignment and Z-statistics kernels
+ *   pieces       [n_pieces][4]   first pair, end pair, first chunk, end chunk:
+ *                the pieces a host input is copied and aligned in
+ *   label_chunks [n_label_chunks + 1][2]  position in `order`, first item:
+ *                the cuts of the label draws and GEMM launches
+ *   items        [n_items][2]    pair, group of 4 x 128 relabellings: the GEMM
+ *                work list, costliest pairs first
+ *   order        [P]             the pairs in the work list's order
+ * The last three are empty unless the path is a tensor-core path.
+ * Errors as hb_perm_test_batched's argument checks. */
+typedef struct {
+    int32_t n_chunks;
+    int32_t n_pieces;
+    int32_t n_label_chunks;
+    int32_t n_items;
+} hb_layout_counts;
+hb_status hb_plan_layout(int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
+                         const hb_opts *opts, hb_layout_counts *counts, int32_t *chunks, int32_t *pieces,
+                         int32_t *label_chunks, int32_t *items, int32_t *order);
+
 /* Route tuning (the paper's Sec. 3.2 leaves the block size and the GEMM
  * route to the implementation; none of them changes a result).  Pair sizes
  * N = n + m fall into HB_ROUTE_BUCKETS buckets: bucket 0 holds N <= 64,

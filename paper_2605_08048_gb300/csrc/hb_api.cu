@@ -1119,6 +1119,59 @@ extern "C" void hb_plan_destroy(hb_plan *q)
     delete q;
 }
 
+extern "C" hb_status hb_plan_layout(int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
+                                    const hb_opts *opts, hb_layout_counts *counts, int32_t *chunks, int32_t *pieces,
+                                    int32_t *label_chunks, int32_t *items, int32_t *order)
+{
+    if (P < 1 || P > (1 << 24)) return fail(HB_ERR_INVALID_ARG, "P = %lld", (long long)P);
+    if (!n || !m || !counts) return fail(HB_ERR_INVALID_ARG, "n, m and counts must be non-NULL");
+    hb_status hs = validate_common(d, dtype);
+    if (hs != HB_OK) return hs;
+    hs = validate_opts(opts);
+    if (hs != HB_OK) return hs;
+    if (opts->path == HB_PATH_AUTO) return fail(HB_ERR_INVALID_ARG, "HB_PATH_AUTO needs a context's route table");
+    Plan pl;
+    hs = make_plan(pl, P, n, m, d, dtype, *opts, false, false);
+    if (hs != HB_OK) return hs;
+    PairSpan sp[ALIGN_PIECES];
+    const int np = piece_spans(pl, ALIGN_PIECES, sp);
+    counts->n_chunks = (int32_t)pl.chunks.size();
+    counts->n_pieces = np;
+    counts->n_label_chunks = pl.nlc;
+    counts->n_items = pl.o.path == HB_PATH_MIXED ? (int32_t)pl.items.size() : 0;
+    if (chunks)
+        for (size_t k = 0; k < pl.chunks.size(); ++k) {
+            const RowChunk &c = pl.chunks[k];
+            int32_t *r = chunks + 4 * k;
+            r[0] = c.pair;
+            r[1] = c.side;
+            r[2] = c.row0;
+            r[3] = c.nrows;
+        }
+    if (pieces)
+        for (int k = 0; k < np; ++k) {
+            int32_t *r = pieces + 4 * k;
+            r[0] = sp[k].p0;
+            r[1] = sp[k].p1;
+            r[2] = sp[k].c0;
+            r[3] = sp[k].c1;
+        }
+    if (label_chunks)
+        for (int k = 0; k <= pl.nlc; ++k) {
+            label_chunks[2 * k] = pl.lc_pair[k];
+            label_chunks[2 * k + 1] = pl.lc_item[k];
+        }
+    if (items && counts->n_items)
+        for (size_t k = 0; k < pl.items.size(); ++k) {
+            items[2 * k] = pl.items[k].pair;
+            items[2 * k + 1] = pl.items[k].tile;
+        }
+    if (order && counts->n_items)
+        for (size_t k = 0; k < pl.order.size(); ++k) order[k] = pl.order[k];
+    g_err.clear();
+    return HB_OK;
+}
+
 static hb_status plan_build(hb_plan *q, int64_t P)
 {
     hb_ctx *c = q->c;

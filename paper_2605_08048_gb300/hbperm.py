@@ -347,6 +347,38 @@ class Plan:
             pass
 
 
+class hb_layout_counts(C.Structure):
+    _fields_ = [("n_chunks", C.c_int32), ("n_pieces", C.c_int32), ("n_label_chunks", C.c_int32),
+                ("n_items", C.c_int32)]
+
+
+def plan_layout(n, m, d: int, dtype, opts: hb_opts) -> dict:
+    """hb_plan_layout: the launch layout of a batched call for these sizes
+    (host computation, no GPU): row chunks [k][pair, side, row0, rows], input
+    pieces [k][p0, p1, c0, c1], label/GEMM chunk cuts [k][order position, first
+    item], work items [k][pair, tile group] and the pair order, as int32
+    numpy arrays."""
+    L = lib()
+    vp = C.c_void_p
+    L.hb_plan_layout.argtypes = [C.c_int64, vp, vp, C.c_int64, C.c_int32, C.POINTER(hb_opts),
+                                 C.POINTER(hb_layout_counts), vp, vp, vp, vp, vp]
+    L.hb_plan_layout.restype = C.c_int
+    na, ma = _sizes(n), _sizes(m)
+    if na.ndim != 1 or na.shape != ma.shape:
+        raise ValueError("n and m must be 1-D with one entry per pair")
+    code = dtype if isinstance(dtype, int) else _dtype_code(torch.empty(0, dtype=dtype))
+    P = len(na)
+    cnt = hb_layout_counts()
+    args = (P, na.ctypes.data, ma.ctypes.data, int(d), code, C.byref(opts), C.byref(cnt))
+    _check(L.hb_plan_layout(*args, None, None, None, None, None))
+    out = {"chunks": np.zeros((cnt.n_chunks, 4), np.int32), "pieces": np.zeros((cnt.n_pieces, 4), np.int32),
+           "label_chunks": np.zeros((cnt.n_label_chunks + 1, 2), np.int32),
+           "items": np.zeros((cnt.n_items, 2), np.int32), "order": np.zeros(P if cnt.n_items else 0, np.int32)}
+    _check(L.hb_plan_layout(*args, *(out[k].ctypes.data if out[k].size else None
+                                     for k in ("chunks", "pieces", "label_chunks", "items", "order"))))
+    return out
+
+
 def autotune(ctx: Context, d: int, dtype, opts: hb_opts, max_N: int = 65536):
     """Times the routes per size bucket and fills the context's route table;
     returns the [ROUTE_BUCKETS][len(ROUTE_PATHS)] wall-clock ms (in
