@@ -35,10 +35,12 @@ def test_header_struct_layouts_match_binding(tmp_path):
     src = tmp_path / "layout.c"
     fields_o = [f for f, _ in H.hb_opts._fields_]
     fields_r = [f for f, _ in H.hb_result._fields_]
+    fields_l = [f for f, _ in H.hb_layout_counts._fields_]
     body = ['#include <stdio.h>', '#include <stddef.h>', '#include "hbperm.h"', "int main(void){",
-            'printf("%zu %zu\\n", sizeof(hb_opts), sizeof(hb_result));']
+            'printf("%zu %zu %zu\\n", sizeof(hb_opts), sizeof(hb_result), sizeof(hb_layout_counts));']
     body += [f'printf("%zu\\n", offsetof(hb_opts, {f}));' for f in fields_o]
     body += [f'printf("%zu\\n", offsetof(hb_result, {f}));' for f in fields_r]
+    body += [f'printf("%zu\\n", offsetof(hb_layout_counts, {f}));' for f in fields_l]
     body += ["return 0;}"]
     src.write_text("\n".join(body))
     exe = tmp_path / "layout"
@@ -46,8 +48,10 @@ def test_header_struct_layouts_match_binding(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     vals = [int(v) for v in out]
     assert vals[0] == ctypes.sizeof(H.hb_opts) and vals[1] == ctypes.sizeof(H.hb_result)
+    assert vals[2] == ctypes.sizeof(H.hb_layout_counts)
     offs = [getattr(H.hb_opts, f).offset for f in fields_o] + [getattr(H.hb_result, f).offset for f in fields_r]
-    assert vals[2:] == offs
+    offs += [getattr(H.hb_layout_counts, f).offset for f in fields_l]
+    assert vals[3:] == offs
 
 
 def test_binding_refuses_without_library(tmp_path, monkeypatch):
