@@ -1166,7 +1166,8 @@ extern "C" hb_status hb_plan_layout(int64_t P, const int64_t *n, const int64_t *
             items[2 * k] = pl.items[k].pair;
             items[2 * k + 1] = pl.items[k].tile;
         }
-    if (order && counts->n_items)
+    // the pair order exists on every tensor-core path, also when no pair has work items
+    if (order && pl.o.path == HB_PATH_MIXED)
         for (size_t k = 0; k < pl.order.size(); ++k) order[k] = pl.order[k];
     g_err.clear();
     return HB_OK;

@@ -90,21 +90,30 @@ extern "C" hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, i
                                       int32_t align, int32_t reflect_side, void *Z_out, double *u_out,
                                       int32_t *skipped, void *stream)
 {
-    if (!X || !Y || !Z_out) return HB_ERR_INVALID_ARG;
-    if (dtype != HB_F32 && dtype != HB_BF16) return HB_ERR_INVALID_ARG;
-    if (reflect_side != 0 && reflect_side != 1) return HB_ERR_INVALID_ARG;
-    if (n < 1 || m < 1 || d < 1) return HB_ERR_INVALID_ARG;
-    if (d > NOALLOC_MAX_D || n + m > NOALLOC_MAX_ROWS) {
-        hb_internal_set_error("hb_align_noalloc: needs d <= 1024 and n + m <= 8192 (fixed 2 MiB device scratch)");
-        return HB_ERR_UNSUPPORTED;
-    }
+    // every return sets the message hb_last_error() reports (cleared on success)
+    auto err = [](hb_status st, const char *msg) {
+        hb_internal_set_error(msg);
+        return st;
+    };
+    if (!X || !Y || !Z_out) return err(HB_ERR_INVALID_ARG, "hb_align_noalloc: X, Y and Z_out must be non-NULL");
+    if (dtype != HB_F32 && dtype != HB_BF16) return err(HB_ERR_INVALID_ARG, "hb_align_noalloc: dtype unknown");
+    if (reflect_side != 0 && reflect_side != 1)
+        return err(HB_ERR_INVALID_ARG, "hb_align_noalloc: reflect_side must be 0 or 1");
+    if (n < 1 || m < 1 || d < 1) return err(HB_ERR_INVALID_ARG, "hb_align_noalloc: n, m and d must be >= 1");
+    if (d > NOALLOC_MAX_D || n + m > NOALLOC_MAX_ROWS)
+        return err(HB_ERR_UNSUPPORTED,
+                   "hb_align_noalloc: needs d <= 1024 and n + m <= 8192 (fixed 2 MiB device scratch)");
     const int nch_x = (int)((n + CHUNK_ROWS - 1) / CHUNK_ROWS), nch_y = (int)((m + CHUNK_ROWS - 1) / CHUNK_ROWS);
     const NoallocLayout L(nch_x + nch_y, (int)d);
-    if (L.total > NOALLOC_SCRATCH_BYTES) return HB_ERR_UNSUPPORTED;
+    if (L.total > NOALLOC_SCRATCH_BYTES)
+        return err(HB_ERR_UNSUPPORTED, "hb_align_noalloc: the request does not fit the 2 MiB device scratch");
 
     // once per device, with that device current: the array's device address
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HB_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return err(HB_ERR_CUDA, "hb_align_noalloc: cudaGetDevice failed or the device index is >= 64");
+    }
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -112,7 +121,7 @@ extern "C" hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, i
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
-                return HB_ERR_CUDA;
+                return err(HB_ERR_CUDA, "hb_align_noalloc: cudaGetSymbolAddress of the scratch array failed");
             }
             g_noalloc_ptr[dev] = (unsigned char *)p;
         }
@@ -157,15 +166,21 @@ extern "C" hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, i
     launch_colsum(meta, chunks, all, (int)d, dtype, part, sums, bad, s);
     launch_axis(meta, all, o, sums, bad, st, u, s);
     launch_reflect(meta, chunks, all, o, st, u, Z_out, nullptr, s);
-    if (cudaGetLastError() != cudaSuccess) return HB_ERR_CUDA;
-    if (u_out && cudaMemcpyAsync(u_out, u, sizeof(double) * (size_t)d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return HB_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return err(HB_ERR_CUDA, "hb_align_noalloc: a kernel launch failed");
+    if (u_out && cudaMemcpyAsync(u_out, u, sizeof(double) * (size_t)d, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return err(HB_ERR_CUDA, "hb_align_noalloc: copy of u failed");
+    }
     if (skipped) {
         PairState hst;
-        if (cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, s) != cudaSuccess) return HB_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
-        if (hst.status != ST_OK) return (hb_status)hst.status;
+        if (cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return err(HB_ERR_CUDA, "hb_align_noalloc: reading the alignment status failed");
+        }
+        if (hst.status != ST_OK) return err((hb_status)hst.status, "hb_align_noalloc: alignment failed (invalid or degenerate input)");
         *skipped = hst.skipped;
     }
+    hb_internal_set_error("");
     return HB_OK;
 }

@@ -373,7 +373,8 @@ def plan_layout(n, m, d: int, dtype, opts: hb_opts) -> dict:
     _check(L.hb_plan_layout(*args, None, None, None, None, None))
     out = {"chunks": np.zeros((cnt.n_chunks, 4), np.int32), "pieces": np.zeros((cnt.n_pieces, 4), np.int32),
            "label_chunks": np.zeros((cnt.n_label_chunks + 1, 2), np.int32),
-           "items": np.zeros((cnt.n_items, 2), np.int32), "order": np.zeros(P if cnt.n_items else 0, np.int32)}
+           "items": np.zeros((cnt.n_items, 2), np.int32),
+           "order": np.zeros(P if opts.path != HB_PATH_FP32_PLAIN else 0, np.int32)}
     _check(L.hb_plan_layout(*args, *(out[k].ctypes.data if out[k].size else None
                                      for k in ("chunks", "pieces", "label_chunks", "items", "order"))))
     return out
