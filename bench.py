@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--B", type=int, default=9999)
     ap.add_argument("--d", type=int, default=768)
-    ap.add_argument("--path", choices=["mixed", "mixed-2sm", "plain"], default="mixed")
+    ap.add_argument("--path", choices=["mixed", "mixed-2sm", "plain"], default="mixed-2sm")
+    ap.add_argument("--s1-max", type=int, default=8192, help="pairs with n + m up to this start with one slice")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -243,6 +244,7 @@ def main():
     n, m = batch.n, batch.m
     ctx = H.Context(local)
     H.set_timing(ctx, True)
+    H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, a.s1_max)
     opts = H.make_opts(B=a.B, seed=1, path=path)
 
     def barrier():
@@ -286,7 +288,7 @@ def main():
     achieved = algo_flops / (gemm_ms / 1000.0) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", 1700.0))
     traffic = None
-    if path == H.HB_PATH_MIXED and a.B == 9999 and a.d == 768:
+    if path == H.HB_PATH_MIXED_2SM and a.B == 9999 and a.d == 768:
         import hashlib
 
         src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2605_08048_gb300", "csrc", "hb_mixed.cu")

@@ -76,16 +76,24 @@ typedef enum { HB_STAT_LOGVOL_VMF = 0, HB_STAT_ONE_MINUS_R2 = 1, HB_STAT_MEAN_CO
  * (Eq. pvalue as printed), or T_b <= T_obs.  Ties count. */
 typedef enum { HB_ALT_TWO_SIDED = 0, HB_ALT_GREATER = 1, HB_ALT_LESS = 2 } hb_alt;
 
-/* HB_PATH_MIXED: exact 16-bit fixed-point slices of Z on tcgen05 tensor
- * cores (BF16 operands, FP32 accumulators in TMEM), wide column tiles (128
- * z-columns per accumulator tile; 64 for FP32 input).  HB_PATH_MIXED_NARROW:
- * the same with half-width column tiles.  HB_PATH_MIXED_2SM: wide tiles on
- * pairs of SMs (tcgen05 cta_group::2, 256 relabellings per MMA, each SM
- * holding half of every Z-slice tile).  HB_PATH_FP32_PLAIN: the paper's
- * Algorithm 2 taken literally (+-1 signs, FP32 SIMT GEMM).  HB_PATH_AUTO:
- * each pair takes the route the context's route table holds for its size
- * (hb_autotune; untuned: HB_PATH_MIXED up to n + m = 65536, the SIMT path
- * above).  All paths give identical results. */
+/* HB_PATH_MIXED: group sums on tcgen05 tensor cores (BF16 operands, FP32
+ * accumulators in TMEM) over exact slices of Z, 256-column accumulator tiles.
+ * BF16 input: each column of a pair is split into two BF16 slices on
+ * power-of-two grids chosen from the column's L1 norm, so that every FP32
+ * accumulator is exact; pairs with n + m up to a limit (HB_OPT_SINGLE_SLICE_MAX_N)
+ * first run the first slice alone (256 z-columns per tile: half the tensor
+ * work) and re-run both slices only for the relabellings that fall inside
+ * that pass's error band.  FP32 input: three fixed-point slices of 64
+ * z-columns per tile.  HB_PATH_MIXED runs single CTAs (one SM per MMA, each
+ * loading its own Z-slice tiles); HB_PATH_MIXED_NARROW the same with
+ * half-width tiles; HB_PATH_MIXED_2SM tcgen05 cta_group::2 on pairs of SMs
+ * (256 relabellings per MMA, each SM loading half of every Z-slice tile, so
+ * half the B bytes per SM: the fastest route on GB300).  No route copies data
+ * by TMA multicast.  HB_PATH_FP32_PLAIN: the paper's Algorithm 2 taken
+ * literally (+-1 signs, FP32 SIMT GEMM).  HB_PATH_AUTO: each pair takes the
+ * route the context's route table holds for its size (hb_autotune; untuned:
+ * HB_PATH_MIXED_2SM up to n + m = 65536, the SIMT path above).  All paths
+ * give identical results. */
 typedef enum {
     HB_PATH_MIXED = 0,
     HB_PATH_FP32_PLAIN = 1,
@@ -193,8 +201,10 @@ void hb_plan_destroy(hb_plan *plan);
  *                the pieces a host input is copied and aligned in
  *   label_chunks [n_label_chunks + 1][2]  position in `order`, first item:
  *                the cuts of the label draws and GEMM launches
- *   items        [n_items][2]    pair, group of 4 x 128 relabellings: the GEMM
- *                work list, costliest pairs first
+ *   items        [n_items][3]    pair, group of 128-relabelling tiles (2 on
+ *                HB_PATH_MIXED_2SM, else 1), mode
+ *                (0 = every slice, 1 = the single-slice pass): the GEMM work
+ *                list, costliest pairs first
  *   order        [P]             the pairs in the work list's order
  * The last three are empty unless the path is a tensor-core path.
  * Errors as hb_perm_test_batched's argument checks. */
@@ -332,6 +342,24 @@ hb_status hb_ctx_set_timing(hb_ctx *ctx, int32_t enable);
  * n_launches (host, nullable) receives the kernel launches of that call.
  * HB_ERR_INVALID_ARG if timing was not enabled for that call. */
 hb_status hb_ctx_stage_times(hb_ctx *ctx, float *ms_out, int32_t *n_launches);
+
+/* Context options (hb_ctx_set_option).  None changes a result.
+ *   HB_OPT_WAIT_LIMIT_NS        wall-clock limit of every device barrier wait of
+ *                               the tensor-core kernels (default 4e9; 1e3..6e10);
+ *                               a wait that runs out ends the call with
+ *                               HB_ERR_TIMEOUT and leaves the context usable
+ *   HB_OPT_SINGLE_SLICE_MAX_N   BF16 input: pairs with n + m <= value start with
+ *                               the single-slice pass (default 8192; 0 = never)
+ *   HB_OPT_TEST_WITHHOLD_ARRIVAL  test hook: 1 = the next tensor-core call on
+ *                               this context withholds one barrier arrival of
+ *                               its first GEMM launch, so that a bounded wait
+ *                               runs out and the call returns HB_ERR_TIMEOUT
+ *                               (the hook then clears itself; plans ignore it)
+ * Options apply to later calls and plans created later. */
+#define HB_OPT_WAIT_LIMIT_NS 1
+#define HB_OPT_SINGLE_SLICE_MAX_N 2
+#define HB_OPT_TEST_WITHHOLD_ARRIVAL 4
+hb_status hb_ctx_set_option(hb_ctx *ctx, int32_t option, int64_t value);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *hb_last_error(void);

@@ -12,8 +12,9 @@
 //       the mixed path
 //   k_zstats_partial / k_zstats_tok / k_zstats_reduce : exact column totals t
 //       of Z and the group-1 sums of the observed split, the band constants,
-//       and (mixed path) the 16/24-bit fixed-point slices of Z in
-//       token-contiguous rows for the tensor-core B operand
+//       and (tensor-core path) the slices of Z in token-contiguous rows for
+//       the tensor-core B operand: two grid slices of the values for BF16
+//       storage (l1_split), three fixed-point slices for FP32 storage
 //   k_tobs   : observed statistic T_obs from the exact sums (Eq. tobs)
 //
 // The FP64 arithmetic uses explicit __d*_rn / __fma_rn intrinsics so that no
@@ -124,6 +125,7 @@ __global__ void k_axis(const PairMeta *__restrict__ meta, int p0, const RunOpts 
         st[p].count = 0ull;
         st[p].rechecked = 0ull;
         st[p].band_max_bits = 0u;
+        st[p].n_gather = 0u;
         skip = 1;
     }
     __syncthreads();
@@ -195,7 +197,8 @@ template <int DT>
 __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__ meta, const RowChunk *__restrict__ chunks,
                                                  int c0, const RunOpts o, const PairState *__restrict__ st,
                                                  const double *__restrict__ u, void *__restrict__ Z,
-                                                 unsigned int *__restrict__ colmax)
+                                                 unsigned int *__restrict__ colmax,
+                                                 unsigned long long *__restrict__ colL1)
 {
     __shared__ float xs[CHUNK_ROWS][RT + 1];
     __shared__ double us[RT];
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
         const double uj = reflect ? up[j] : 0.0;
         const float uh = __double2float_rn(uj), ul = __double2float_rn(__dsub_rn(uj, (double)uh));
         const float auh = fabsf(uh);
-        float mx = 0.0f;
+        float mx = 0.0f, l1 = 0.0f;  // column maximum and sum of |z| (rounded up) over the chunk
         for (int rb = 0; rb < ch.nrows; rb += RB) {
         uint32_t xv[RB];
 #pragma unroll
@@ -362,9 +365,13 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
                 zf = __uint_as_float(xb);
             }
             mx = fmaxf(mx, fabsf(zf));
+            l1 = __fadd_ru(l1, fabsf(zf));
         }
         }
         if (colmax) atomicMax(colmax + (int64_t)ch.pair * o.d_pad + j, __float_as_uint(mx));
+        // an upper bound of the column's L1 norm in units of 2^-40 (integer atomics:
+        // exact and order-free, so the slice grids do not depend on the schedule)
+        if (colL1) atomicAdd(colL1 + (int64_t)ch.pair * o.d_pad + j, __float2ull_ru(__fmul_rn(l1, 0x1p40f)));
     }
 }
 
@@ -413,17 +420,16 @@ __device__ __forceinline__ void fixed_split(float z, float qh, int S, float &hi,
     }
 }
 
-// row of the slice matrix holding slice s of column j (tiles of cw columns)
-__device__ __forceinline__ int64_t slice_row(int j, int s, int S, int cw)
-{
-    return (int64_t)(j / cw) * S * cw + (int64_t)s * cw + (j % cw);
-}
+// The slice matrix holds slice s of column j in row s * d_pad + j, tokens
+// contiguous (all pairs' tokens side by side, each pair from its z_row).
+__device__ __forceinline__ int64_t slice_row(int j, int s, int d_pad) { return (int64_t)s * d_pad + j; }
 
 // One block (256 threads) per row chunk, tiles of ZS_T columns.  Phase A:
 // thread (column, 16-row part) reads its values (coalesced across columns),
-// adds them exactly to the column totals, splits each once into the
-// fixed-point slices (staged transposed in shared memory) and sums the
-// residuals; phase B stores the slices token-contiguous.
+// adds them exactly to the column totals, splits each once into its slices
+// (staged transposed in shared memory) and sums the residuals; phase B stores
+// the slices token-contiguous.  FP32 storage: three fixed-point slices of
+// the column's scale; BF16 storage: the two grid slices (l1_split).
 constexpr int ZS_T = 32;
 constexpr int ZS_PARTS = 256 / ZS_T;               // 8 parts of 16 rows
 constexpr int ZS_ROWS = CHUNK_ROWS / ZS_PARTS;     // 16
@@ -434,12 +440,14 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
                                                         const RunOpts o,
                                                         const PairState *__restrict__ st, const void *__restrict__ Z,
                                                         const unsigned int *__restrict__ colmax,
+                                                        const unsigned long long *__restrict__ colL1,
                                                         i128 *__restrict__ tpart, float *__restrict__ cpart,
+                                                        float *__restrict__ cpart1,
                                                         unsigned short *__restrict__ zq, int64_t zq_ld)
 {
     __shared__ unsigned short sq[3][ZS_T][CHUNK_ROWS + 2];
     __shared__ i128 acc_s[ZS_PARTS][ZS_T];
-    __shared__ float cacc_s[ZS_PARTS][ZS_T];
+    __shared__ float cacc_s[ZS_PARTS][ZS_T], cacc1_s[ZS_PARTS][ZS_T];
     const int ci = c0 + (int)blockIdx.x;  // chunk index
     const RowChunk ch = chunks[ci];
     const PairMeta pm = meta[ch.pair];
@@ -458,9 +466,11 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
         const int j = j0 + jj;
         const unsigned int mb = j < d ? colmax[(int64_t)ch.pair * o.d_pad + j] : 0u;
         const float qh = qhi_from_max(mb);
+        L1Grid G{};
+        if (mixed && DT == DT_BF16) G = l1_grid(j < d ? colL1[(int64_t)ch.pair * o.d_pad + j] : 0ull, pm.N);
         WinAcc wa;
         wa.init(col_bound_exp(mb));
-        float cacc = 0.0f;
+        float cacc = 0.0f, cacc1 = 0.0f;
         const int r0 = part * ZS_ROWS, nr = max(0, min(ch.nrows - r0, ZS_ROWS));
         // this thread's values first (all loads in flight), then the arithmetic
         uint32_t bv[ZS_ROWS];
@@ -473,7 +483,15 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
             const uint32_t b = bv[k];
             wa.add(b);
             const float z = __uint_as_float(b);
-            if (mixed) {
+            if (mixed && DT == DT_BF16) {
+                float k1, k2, r1, r2;
+                l1_split(z, G, k1, k2, r1, r2);
+                cacc = __fadd_ru(cacc, fabsf(r2));
+                cacc1 = __fadd_ru(cacc1, fabsf(r1));
+                // k1 g and k2 g2 have at most 8 significant bits: BF16 exactly
+                sq[0][jj][r] = (unsigned short)(__float_as_uint(__fmul_rn(k1, G.g)) >> 16);
+                sq[1][jj][r] = (unsigned short)(__float_as_uint(__fmul_rn(k2, G.g2)) >> 16);
+            } else if (mixed) {
                 float hi, lo, lo2, res;
                 fixed_split(z, qh, S, hi, lo, lo2, res);
                 cacc = __fadd_ru(cacc, fabsf(res));
@@ -486,13 +504,14 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
         }
         acc_s[part][jj] = wa.total();
         cacc_s[part][jj] = cacc;
+        cacc1_s[part][jj] = cacc1;
         __syncthreads();
         if (mixed) {
             // warp per column, lanes along tokens: token-contiguous stores
             const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
             for (int c = wp; c < ZS_T && j0 + c < d; c += (int)(blockDim.x >> 5)) {
                 for (int s = 0; s < S; ++s) {
-                    unsigned short *dst = zq + slice_row(j0 + c, s, S, o.cw) * zq_ld + pm.z_row;
+                    unsigned short *dst = zq + slice_row(j0 + c, s, o.d_pad) * zq_ld + pm.z_row;
                     for (int r = ln; r < ch.nrows; r += 32) dst[tok0 + r] = sq[s][c][r];
                     for (int k = ln; k < npad; k += 32) dst[pm.N + k] = 0;
                 }
@@ -500,29 +519,31 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
         }
         if (threadIdx.x < ZS_T && j0 + threadIdx.x < d) {
             i128 a = 0;
-            float c = 0.0f;
+            float c = 0.0f, c1 = 0.0f;
             for (int q = 0; q < ZS_PARTS; ++q) {
                 a += acc_s[q][threadIdx.x];
                 c = __fadd_ru(c, cacc_s[q][threadIdx.x]);
+                c1 = __fadd_ru(c1, cacc1_s[q][threadIdx.x]);
             }
             tpart[(int64_t)ci * d + j0 + threadIdx.x] = a;
             cpart[(int64_t)ci * d + j0 + threadIdx.x] = c;
+            cpart1[(int64_t)ci * d + j0 + threadIdx.x] = c1;
         }
         __syncthreads();
     }
 }
 
-// The same outputs for the tensor-core path on BF16 storage with two slices
-// and d a multiple of 8, with lanes along tokens.  Warp w takes the 8-column
-// groups w, w + 8, ... ; lane l takes the four consecutive token positions
+// The same outputs for the tensor-core path on BF16 storage with d a
+// multiple of 8, with lanes along tokens.  Warp w takes the 8-column groups
+// w, w + 8, ... ; lane l takes the four consecutive token positions
 // 4l .. 4l + 3 of the chunk, position q being token tok0 - g + q with
 // g = tok0 mod 4, so that a lane's four values of one slice column leave in
-// one aligned 8-byte store (the host keeps g + nrows <= 128).  Where an
-// element's slices are exact (residual 0), its value hi q_hi + lo q_lo enters
-// the column total through integer sums of hi and lo (a warp reduction per
-// column); the few other elements are added exactly as values, with the same
-// rule as the oracle (|v| < 2^-64 counts as 0), so every chunk total is the
-// exact sum of its values.
+// one aligned 8-byte store (the host keeps g + nrows <= 128).  The column
+// total is k_sum g + k2_sum g2 (integer warp sums of the slice multiples)
+// plus the rare nonzero second residuals added exactly out of line (columns
+// outside the split range add every value exactly, with the oracle's rule
+// that |v| < 2^-64 counts as 0), so every chunk total is the exact sum of its
+// values.
 __device__ __forceinline__ i128 warp_sum_i128(i128 v)
 {
 #pragma unroll
@@ -544,7 +565,7 @@ __device__ __forceinline__ float warp_sum_ru(float v)
     return v;
 }
 
-// Exact fixed-point value (unit 2^-87) of a residual of the split: a nonzero
+// Exact fixed-point value (unit 2^-87) of a second residual: a nonzero
 // residual of a value z >= 2^-64 is a multiple of z's last bit, so >= 2^-71
 // and a multiple of 2^-87 (the right shift below drops only zero bits).
 __device__ __forceinline__ i128 fixed_from_residual(uint32_t b)
@@ -557,53 +578,41 @@ __device__ __forceinline__ i128 fixed_from_residual(uint32_t b)
 }
 
 // The exact part of one column of a warp's 128 positions, called by the whole
-// warp (out of line: rare).  Split columns (fast): the residuals of the values
-// >= 2^-64 exactly (q_hi hi + q_lo lo are already in the integer sums);
-// otherwise every value exactly (|v| < 2^-64 counts as 0, as in the oracle).
-// Both sum the residuals rounded up.
-struct SlowCol {
-    i128 sum;
-    float ca;
-};
-
-__device__ __noinline__ SlowCol zs_slow_column(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, bool high,
-                                               unsigned int okm, bool fast, float inv, float qh, float inv_l,
-                                               float ql)
+// warp (out of line: rare): split columns add their second residuals, the
+// others every value (|v| < 2^-64 counts as 0).
+__device__ __noinline__ i128 zs_slow_column(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, bool high,
+                                            unsigned int okm, const L1Grid G)
 {
     i128 sl = 0;
-    float ca = 0.0f;
     const uint32_t ws[4] = {w0, w1, w2, w3};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (!((okm >> i) & 1u)) continue;
         const uint32_t bb = high ? (ws[i] & 0xffff0000u) : (ws[i] << 16);
-        const float z = __uint_as_float(bb);
-        const float hi = rintf(__fmul_rn(z, inv));
-        const float w = __fmaf_rn(-hi, qh, z);
-        const float lo = rintf(__fmul_rn(w, inv_l));
-        const float res = __fmaf_rn(-lo, ql, w);
-        if (!fast) sl += fixed_from_f32bits(bb);
-        else if (res != 0.0f && ((bb >> 23) & 0xffu) >= 63u) sl += fixed_from_residual(__float_as_uint(res));
-        ca = __fadd_ru(ca, fabsf(res));
+        if (!G.split) {
+            sl += fixed_from_f32bits(bb);
+        } else {
+            float k, k2, r1, r2;
+            l1_split(__uint_as_float(bb), G, k, k2, r1, r2);
+            if (r2 != 0.0f) sl += fixed_from_residual(__float_as_uint(r2));
+        }
     }
-    SlowCol r;
-    r.sum = warp_sum_i128(sl);
-    r.ca = warp_sum_ru(ca);
-    return r;
+    return warp_sum_i128(sl);
 }
 
 __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restrict__ meta,
                                                     const RowChunk *__restrict__ chunks, int c0, const RunOpts o,
                                                     const PairState *__restrict__ st, const uint4 *__restrict__ Z,
-                                                    const unsigned int *__restrict__ colmax,
+                                                    const unsigned long long *__restrict__ colL1,
                                                     i128 *__restrict__ tpart, float *__restrict__ cpart,
+                                                    float *__restrict__ cpart1,
                                                     unsigned short *__restrict__ zq, int64_t zq_ld)
 {
     const int ci = c0 + (int)blockIdx.x;  // chunk index
     const RowChunk ch = chunks[ci];
     const PairMeta pm = meta[ch.pair];
     if (st[ch.pair].status != ST_OK) return;
-    const int d = o.d, cw = o.cw;
+    const int d = o.d, d_pad = o.d_pad;
     const int64_t tok0 = (ch.side ? pm.n : 0) + ch.row0;  // token index within the pair
     const int g = (int)(tok0 & 3);
     const bool last = ch.side == 1 && ch.row0 + ch.nrows == pm.m;
@@ -616,64 +625,56 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
     const bool full = ok[0] && ok[1] && ok[2] && ok[3];
     const unsigned int okm = (ok[0] ? 1u : 0u) | (ok[1] ? 2u : 0u) | (ok[2] ? 4u : 0u) | (ok[3] ? 8u : 0u);
     const int64_t tq = pm.z_row + tok0 - g + 4 * ln;  // slice-row offset of the lane's first position
-    const unsigned int *cm = colmax + (int64_t)ch.pair * o.d_pad;
+    const unsigned long long *cl = colL1 + (int64_t)ch.pair * d_pad;
     const int d16 = d / 8;  // 16-byte units per row
     // row rb of the chunk (the lane's first position) in 16-byte units; only rows
     // with ok[i] are read
     const int64_t zr = (pm.z_row + tok0 + rb) * d16;
-    const int lcw = __ffs(cw) - 1;  // cw is a power of two
+    const int64_t lo_off = (int64_t)d_pad * zq_ld;  // second slice: d_pad rows further
 
     for (int c8 = wp; c8 < d16; c8 += 8) {
         const int j = 8 * c8;
         uint4 v[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] = ok[i] ? __ldg(Z + zr + i * d16 + c8) : make_uint4(0u, 0u, 0u, 0u);
-        // the 8 columns lie in one tile of cw columns: slice s of column j + e is row base + s cw + e
-        const int64_t base = ((int64_t)(j >> lcw) << (lcw + 1)) + (j & (cw - 1));
-        unsigned short *dh = zq + base * zq_ld + tq;
-        unsigned short *dl = dh + ((int64_t)zq_ld << lcw);
-        // lane e < 8 keeps column j + e's reductions for the group's epilogue
-        int my_ih = 0, my_il = 0, my_E = 0;
-        bool my_fast = false;
+        unsigned short *dh = zq + (int64_t)j * zq_ld + tq;
+        // lane e < 8 keeps column j + e's reductions
+        int my_ik = 0, my_ik2 = 0, my_eg = 0, my_eg2 = 0;
+        bool my_split = false;
         i128 my_slow = 0;
-        float my_ca = 0.0f;
-        const uint4 m0 = __ldg(reinterpret_cast<const uint4 *>(cm + j));
-        const uint4 m1 = __ldg(reinterpret_cast<const uint4 *>(cm + j) + 1);
+        float my_c = 0.0f, my_c1 = 0.0f;
+        const ulonglong2 l01 = __ldg(reinterpret_cast<const ulonglong2 *>(cl + j));
+        const ulonglong2 l23 = __ldg(reinterpret_cast<const ulonglong2 *>(cl + j) + 1);
+        const ulonglong2 l45 = __ldg(reinterpret_cast<const ulonglong2 *>(cl + j) + 2);
+        const ulonglong2 l67 = __ldg(reinterpret_cast<const ulonglong2 *>(cl + j) + 3);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const unsigned int mb = e == 0 ? m0.x : e == 1 ? m0.y : e == 2 ? m0.z : e == 3 ? m0.w
-                                  : e == 4 ? m1.x : e == 5 ? m1.y : e == 6 ? m1.z : m1.w;
-            const int E = col_bound_exp(mb);
-            // split range: q_hi = 2^(E-8), its reciprocal and q_lo = q_hi/512 normal FP32
-            // numbers (always so for valid inputs unless the column is all zero or below
-            // 2^-100); integer sums: residual-free values are then >= 2^-64 or 0
-            const bool split = mb != 0u && E >= -100 && E <= 100;
-            const bool fast = split && E >= -46;
-            // outside the split range the slices are 0 (reciprocals 0) and the residual is z
-            const int Es = split ? E : 8;
-            const float qh = __int_as_float((Es - 8 + 127) << 23), ql = qh * (1.0f / 512.0f);
-            const float inv = split ? __int_as_float((127 - (Es - 8)) << 23) : 0.0f, inv_l = inv * 512.0f;
-            float hf[4], lf[4];
-            float shi = 0.0f, slo = 0.0f, racc = 0.0f;
+            const unsigned long long lb = e == 0 ? l01.x : e == 1 ? l01.y : e == 2 ? l23.x : e == 3 ? l23.y
+                                        : e == 4 ? l45.x : e == 5 ? l45.y : e == 6 ? l67.x : l67.y;
+            const L1Grid G = l1_grid(lb, pm.N);
+            float kf[4], k2f[4];
+            int sk = 0, sk2 = 0;
+            float ra1 = 0.0f, ra2 = 0.0f;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const uint32_t wd = (e >> 1) == 0 ? v[i].x : (e >> 1) == 1 ? v[i].y : (e >> 1) == 2 ? v[i].z : v[i].w;
                 const float z = __uint_as_float((e & 1) ? (wd & 0xffff0000u) : (wd << 16));  // 0 where !ok
-                // exact steps: power-of-two scalings and exact remainders
-                hf[i] = rintf(__fmul_rn(z, inv));
-                const float w = __fmaf_rn(-hf[i], qh, z);
-                lf[i] = rintf(__fmul_rn(w, inv_l));
-                const float res = __fmaf_rn(-lf[i], ql, w);
-                shi += hf[i];  // exact: integers, |sum| <= 1024
-                slo += lf[i];
-                racc += fabsf(res);  // 0 iff every residual is 0
+                float r1, r2;
+                l1_split(z, G, kf[i], k2f[i], r1, r2);
+                sk += __float2int_rz(kf[i]);  // |k| <= 2^24: exact
+                sk2 += __float2int_rz(k2f[i]);
+                ra1 = __fadd_ru(ra1, fabsf(r1));
+                ra2 = __fadd_ru(ra2, fabsf(r2));  // 0 iff every second residual is 0
+                kf[i] = __fmul_rn(kf[i], G.g);    // the slice values (exact)
+                k2f[i] = __fmul_rn(k2f[i], G.g2);
             }
-            // hi and lo are integers of magnitude <= 256: the high halves of their FP32 bits
-            // are their BF16 bits
-            const uint32_t hp0 = __byte_perm(__float_as_uint(hf[0]), __float_as_uint(hf[1]), 0x7632);
-            const uint32_t hp1 = __byte_perm(__float_as_uint(hf[2]), __float_as_uint(hf[3]), 0x7632);
-            const uint32_t lp0 = __byte_perm(__float_as_uint(lf[0]), __float_as_uint(lf[1]), 0x7632);
-            const uint32_t lp1 = __byte_perm(__float_as_uint(lf[2]), __float_as_uint(lf[3]), 0x7632);
+            // the slice values have at most 8 significant bits: the high halves of
+            // their FP32 bits are their BF16 bits
+            const uint32_t hp0 = __byte_perm(__float_as_uint(kf[0]), __float_as_uint(kf[1]), 0x7632);
+            const uint32_t hp1 = __byte_perm(__float_as_uint(kf[2]), __float_as_uint(kf[3]), 0x7632);
+            const uint32_t lp0 = __byte_perm(__float_as_uint(k2f[0]), __float_as_uint(k2f[1]), 0x7632);
+            const uint32_t lp1 = __byte_perm(__float_as_uint(k2f[2]), __float_as_uint(k2f[3]), 0x7632);
+            unsigned short *dl = dh + lo_off;
             if (full) {
                 *reinterpret_cast<uint2 *>(dh) = make_uint2(hp0, hp1);
                 *reinterpret_cast<uint2 *>(dl) = make_uint2(lp0, lp1);
@@ -687,37 +688,41 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
                     }
             }
             dh += zq_ld;
-            dl += zq_ld;
-            const int ih = __reduce_add_sync(0xffffffffu, __float2int_rz(shi));
-            const int il = __reduce_add_sync(0xffffffffu, __float2int_rz(slo));
-            if (ln == e) {
-                my_ih = ih;
-                my_il = il;
-                my_E = E;
-                my_fast = fast;
-            }
-            if (__any_sync(0xffffffffu, !fast || racc != 0.0f)) {
+            const int ik = __reduce_add_sync(0xffffffffu, sk);
+            const int ik2 = __reduce_add_sync(0xffffffffu, sk2);
+            const float c1 = __any_sync(0xffffffffu, ra1 != 0.0f) ? warp_sum_ru(ra1) : 0.0f;
+            float c2 = 0.0f;
+            i128 slow = 0;
+            if (__any_sync(0xffffffffu, !G.split || ra2 != 0.0f)) {
+                c2 = warp_sum_ru(ra2);
                 const uint32_t w0 = (e >> 1) == 0 ? v[0].x : (e >> 1) == 1 ? v[0].y : (e >> 1) == 2 ? v[0].z : v[0].w;
                 const uint32_t w1 = (e >> 1) == 0 ? v[1].x : (e >> 1) == 1 ? v[1].y : (e >> 1) == 2 ? v[1].z : v[1].w;
                 const uint32_t w2 = (e >> 1) == 0 ? v[2].x : (e >> 1) == 1 ? v[2].y : (e >> 1) == 2 ? v[2].z : v[2].w;
                 const uint32_t w3 = (e >> 1) == 0 ? v[3].x : (e >> 1) == 1 ? v[3].y : (e >> 1) == 2 ? v[3].z : v[3].w;
-                const SlowCol sc = zs_slow_column(w0, w1, w2, w3, (e & 1) != 0, okm, fast, inv, qh, inv_l, ql);
-                if (ln == e) {
-                    my_slow = sc.sum;
-                    my_ca = sc.ca;
-                }
+                slow = zs_slow_column(w0, w1, w2, w3, (e & 1) != 0, okm, G);
+            }
+            if (ln == e) {
+                my_ik = ik;
+                my_ik2 = ik2;
+                my_eg = G.eg;
+                my_eg2 = G.eg2;
+                my_split = G.split;
+                my_slow = slow;
+                my_c = c2;
+                my_c1 = c1;
             }
         }
         if (ln < 8) {
             i128 tot = my_slow;
-            if (my_fast) tot += ((i128)my_ih << (my_E + 79)) + ((i128)my_il << (my_E + 70));
+            if (my_split) tot += ((i128)my_ik << (my_eg + 87)) + ((i128)my_ik2 << (my_eg2 + 87));
             tpart[(int64_t)ci * d + j + ln] = tot;
-            cpart[(int64_t)ci * d + j + ln] = my_ca;
+            cpart[(int64_t)ci * d + j + ln] = my_c;
+            cpart1[(int64_t)ci * d + j + ln] = my_c1;
         }
         // the last chunk of the pair also zero-fills the padded tokens of the slices
         for (int k = ln; k < 16 * npad; k += 32) {
             const int e = k / (2 * npad), s = (k / npad) & 1, t = k % npad;
-            zq[(base + s * cw + e) * zq_ld + pm.z_row + pm.N + t] = 0;
+            zq[slice_row(j + e, s, d_pad) * zq_ld + pm.z_row + pm.N + t] = 0;
         }
     }
 }
@@ -727,7 +732,8 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
 __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p1, const RunOpts o,
                                 const PairState *__restrict__ st, const unsigned int *__restrict__ colmax,
                                 const i128 *__restrict__ tpart, const float *__restrict__ cpart,
-                                i128 *__restrict__ t_ex, i128 *__restrict__ s1o, ColConst *__restrict__ cc)
+                                const float *__restrict__ cpart1, i128 *__restrict__ t_ex, i128 *__restrict__ s1o,
+                                ColConst *__restrict__ cc)
 {
     const int d = o.d;
     const int64_t idx = (int64_t)p0 * o.d_pad + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -744,19 +750,22 @@ __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p
         return;
     }
     i128 a = 0, ax = 0;
-    float csum = 0.0f;
+    float csum = 0.0f, csum1 = 0.0f;
     for (int k = 0; k < pm.nchunk_x + pm.nchunk_y; ++k) {
         const int64_t q = (int64_t)(pm.chunk0 + k) * d + j;
         a += tpart[q];
         if (k < pm.nchunk_x) ax += tpart[q];
         csum = __fadd_ru(csum, cpart[q]);
+        if (o.path == 0 && o.dtype == DT_BF16) csum1 = __fadd_ru(csum1, cpart1[q]);
     }
     t_ex[(int64_t)p * d + j] = a;
     s1o[(int64_t)p * d + j] = ax;
     c.t = __double2float_rn(fixed_to_f64(a));
     if (o.path == 0) {
-        c.q_hi = qhi_from_max(colmax[idx]);
-        c.c = csum;  // sum of |residuals| of the fixed-point slices
+        // FP32 storage: fixed-point slices of scale 2^(E-8); BF16: the slices hold values
+        c.q_hi = o.dtype == DT_BF16 ? 1.0f : qhi_from_max(colmax[idx]);
+        c.c = csum;    // sum of |residuals| of all slices
+        c.c1 = csum1;  // BF16: sum of |residuals| of the first slice alone
     } else {
         // sequential FP32 accumulation over K = N_pad tokens: gamma_K = K u / (1 - K u)
         const float K = (float)pm.N_pad;
@@ -781,8 +790,8 @@ __global__ void k_tobs(const PairMeta *__restrict__ meta, int p0, const RunOpts 
     const int d = o.d;
     double *a = sm_tobs, *b = sm_tobs + d;
     __shared__ double q[2];
-    __shared__ float red[2][64];
-    float tn = 0.0f, c2 = 0.0f;
+    __shared__ float red[3][64];
+    float tn = 0.0f, c2 = 0.0f, c21 = 0.0f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const i128 x = s1o[(int64_t)p * d + j];
         a[j] = fixed_to_f64(x);
@@ -790,9 +799,11 @@ __global__ void k_tobs(const PairMeta *__restrict__ meta, int p0, const RunOpts 
         const ColConst c = cc[(int64_t)p * o.d_pad + j];
         tn = fmaf(c.t, c.t, tn);
         c2 = __fmaf_ru(c.c, c.c, c2);
+        c21 = __fmaf_ru(c.c1, c.c1, c21);
     }
     red[0][threadIdx.x] = tn;
     red[1][threadIdx.x] = c2;
+    red[2][threadIdx.x] = c21;
     __syncthreads();
     if (threadIdx.x == 0 || threadIdx.x == 32) {
         const double *v = threadIdx.x ? b : a;
@@ -802,10 +813,11 @@ __global__ void k_tobs(const PairMeta *__restrict__ meta, int p0, const RunOpts 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float T = 0.0f, C = 0.0f;
+        float T = 0.0f, C = 0.0f, C1 = 0.0f;
         for (int k = 0; k < 64; ++k) {
             T += red[0][k];
             C = __fadd_ru(C, red[1][k]);
+            C1 = __fadd_ru(C1, red[2][k]);
         }
         const double n = (double)pm.n, m = (double)pm.m, dd = (double)d;
         const double A1 = group_value_f64(o.stat, q[0], n, dd);
@@ -818,6 +830,7 @@ __global__ void k_tobs(const PairMeta *__restrict__ meta, int p0, const RunOpts 
         s.ry = __dsqrt_rn(__ddiv_rn(q[1], __dmul_rn(m, m)));
         s.tnorm = sqrtf(T) * (1.0f + 1e-4f);
         s.sumc2 = C * (1.0f + 1e-4f);
+        s.sumc2_1 = C1 * (1.0f + 1e-4f);
         if (o.stat == STAT_LOGVOL &&
             (!(q[0] > 0.0) || !(q[1] > 0.0) || !(A1 < INFINITY) || !(A2 < INFINITY)))
             s.status = ST_DEGENERATE;
@@ -848,30 +861,33 @@ void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, con
 }
 
 void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
-                    const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st)
+                    const PairState *pst, const double *u, void *Z, unsigned int *colmax,
+                    unsigned long long *colL1, cudaStream_t st)
 {
     if (sp.c1 <= sp.c0) return;
     const unsigned nc = (unsigned)(sp.c1 - sp.c0);
-    if (o.dtype == DT_F32) k_reflect<DT_F32><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax);
-    else k_reflect<DT_BF16><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax);
+    if (o.dtype == DT_F32) k_reflect<DT_F32><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax, colL1);
+    else k_reflect<DT_BF16><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax, colL1);
 }
 
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
-                   const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
-                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
-                   cudaStream_t st)
+                   const PairState *pst, const void *Z, const unsigned int *colmax,
+                   const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,
+                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout, cudaStream_t st)
 {
     if (sp.c1 <= sp.c0 || sp.p1 <= sp.p0) return;
     const unsigned nc = (unsigned)(sp.c1 - sp.c0);
     if (o.dtype == DT_F32)
-        k_zstats_partial<DT_F32><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
+        k_zstats_partial<DT_F32><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, colL1, tpart, cpart,
+                                                     cpart1, zq, zq_ld);
     else if (tok_layout)
-        k_zstats_tok<<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, static_cast<const uint4 *>(Z), colmax, tpart,
-                                         cpart, zq, zq_ld);
+        k_zstats_tok<<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, static_cast<const uint4 *>(Z), colL1, tpart,
+                                         cpart, cpart1, zq, zq_ld);
     else
-        k_zstats_partial<DT_BF16><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, tpart, cpart, zq, zq_ld);
-    k_zstats_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * o.d_pad, 256), 256, 0, st>>>(meta, sp.p0, sp.p1, o, pst, colmax,
-                                                                                   tpart, cpart, t_ex, s1o, cc);
+        k_zstats_partial<DT_BF16><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, colL1, tpart, cpart,
+                                                      cpart1, zq, zq_ld);
+    k_zstats_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * o.d_pad, 256), 256, 0, st>>>(
+        meta, sp.p0, sp.p1, o, pst, colmax, tpart, cpart, cpart1, t_ex, s1o, cc);
 }
 
 void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,

@@ -72,7 +72,7 @@ struct hb_ctx {
     bool timing = false;
     bool last_timed = false;
     cudaEvent_t tev[7] = {};
-    cudaEvent_t gev[2 * LABEL_CHUNKS] = {};  // around each GEMM launch
+    cudaEvent_t gev[2 * (LABEL_CHUNKS + 1)] = {};  // around each GEMM launch (and the gathered pass)
     float last_ms[7] = {};
     int last_launches = 0;
     // Streams of a call: the caller's stream forks into `main` (highest
@@ -92,6 +92,10 @@ struct hb_ctx {
     // relabelling statistics of hb_null_quantiles
     void *tbuf = nullptr;
     size_t tbuf_cap = 0;
+    // options (hb_ctx_set_option)
+    uint64_t wait_ns = 4000000000ull;  // limit of every device barrier wait
+    int32_t s1_max = 8192;             // BF16: pairs with n + m <= s1_max start with the single-slice pass
+    int32_t withhold = 0;              // test hook: the next tensor-core call withholds one barrier arrival
 };
 
 extern "C" void hb_ctx_destroy(hb_ctx *c);
@@ -117,7 +121,7 @@ extern "C" hb_status hb_ctx_create(hb_ctx **out, int device)
     CK(cudaSetDevice(device));
     hb_ctx *c = new hb_ctx();
     c->device = device;
-    for (int k = 0; k < HB_ROUTE_BUCKETS; ++k) c->route[k] = k <= 10 ? HB_PATH_MIXED : HB_PATH_FP32_PLAIN;
+    for (int k = 0; k < HB_ROUTE_BUCKETS; ++k) c->route[k] = k <= 10 ? HB_PATH_MIXED_2SM : HB_PATH_FP32_PLAIN;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     int prio_least = 0, prio_greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
@@ -236,9 +240,29 @@ static int64_t binom64(int64_t N, int64_t k)
 
 static inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Context options a plan is built with (defaults without a context).
+struct CtxOpts {
+    uint64_t wait_ns = 4000000000ull;
+    int32_t s1_max = 8192;
+    int32_t withhold = 0;
+};
+
+static CtxOpts ctx_opts(const hb_ctx *c)
+{
+    CtxOpts k;
+    k.wait_ns = c->wait_ns;
+    k.s1_max = c->s1_max;
+    k.withhold = c->withhold;
+    return k;
+}
+
 struct Plan {
     int P;
     RunOpts o;
+    CtxOpts k;
+    int cl = 1;       // tensor-core path: CTAs per work item (2 for CTA pairs)
+    int n_single = 0; // work items of the single-slice pass
+    int64_t total_gl = 0;  // entries of the relabelling lists of the gathered pass
     std::vector<PairMeta> meta;
     std::vector<RowChunk> chunks;
     std::vector<int> init_bad;
@@ -302,16 +326,17 @@ static int32_t route_for_batch(const hb_ctx *c, int64_t P, const int64_t *n, con
         if (r == HB_PATH_FP32_PLAIN && n[p] + m[p] > 65536) return HB_PATH_FP32_PLAIN;
         rows[r] += n[p] + m[p];
     }
-    int32_t best = HB_PATH_MIXED;
+    int32_t best = HB_PATH_MIXED_2SM;
     for (int32_t r = 0; r < 5; ++r)
         if (r != HB_PATH_AUTO && rows[r] > rows[best]) best = r;
     return best;
 }
 
 static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t *m, int64_t d, int32_t dtype,
-                           const hb_opts &op, bool align_only, bool want_T)
+                           const hb_opts &op, bool align_only, bool want_T, const CtxOpts &k = CtxOpts())
 {
     pl.P = (int)P;
+    pl.k = k;
     RunOpts &o = pl.o;
     memset(&o, 0, sizeof o);
     o.seed = op.seed;
@@ -330,12 +355,18 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
     o.dtype = dtype;
     o.want_T = want_T ? 1 : 0;
     if (o.path == HB_PATH_MIXED) {
+        // accumulator tiles of nacc columns: BF16 two grid slices of cw columns (the
+        // single-slice pass covers 2 cw columns per tile), FP32 three fixed-point slices
         o.slices = dtype == HB_F32 ? 3 : 2;
         o.cw = (o.slices == 2 ? 128 : 64) >> (narrow ? 1 : 0);
-        o.d_pad = (int)rup(d, o.cw);
+        o.nacc = o.slices * o.cw;
+        o.d_pad = (int)rup(d, dtype == HB_F32 ? o.cw : 2 * o.cw);
+        o.s1_max = dtype == HB_F32 ? 0 : k.s1_max;
+        pl.cl = o.cg == 2 ? 2 : 1;
     } else {
         o.slices = 0;
         o.cw = 128;
+        o.nacc = 0;
         o.d_pad = (int)d;
     }
     pl.meta.resize(P);
@@ -363,10 +394,12 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         pm.W = (int)((N + 31) / 32);
         if (!align_only) {
             pm.B = op.exhaustive ? binom64(N, np) : op.B;
-            // the mixed path works on groups of MIXED_CLUSTER tiles of 128 relabellings
-            pm.B_pad = (int)rup(pm.B, o.path == HB_PATH_MIXED ? 128 * MIXED_CLUSTER : 128);
+            // the tensor-core path works on groups of cl tiles of 128 relabellings
+            pm.B_pad = (int)rup(pm.B, o.path == HB_PATH_MIXED ? 128 * pl.cl : 128);
             pm.lab_off = lab;
             lab += (int64_t)pm.W * pm.B_pad;
+            pm.g_off = pl.total_gl;
+            pl.total_gl += pm.B_pad;
             pm.T_off = want_T ? tb : -1;
             tb += pm.B;
             if (np < 2 || mp < 2) pl.init_bad[p] = 2;
@@ -391,14 +424,21 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
     pl.total_label_words = lab;
     pl.total_B = tb;
     pl.items.clear();
+    pl.n_single = 0;
     if (!align_only && o.path == HB_PATH_MIXED) {
         std::vector<int> order(P);
         for (int64_t p = 0; p < P; ++p) order[p] = (int)p;
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return pl.meta[a].N_pad > pl.meta[b].N_pad; });
+        // BF16 pairs up to s1_max tokens start with the single-slice pass (the two-slice
+        // pass then runs on the relabellings it leaves in its band); larger ones, whose
+        // single-slice band is wide, and FP32 input take every slice at once
         for (int p : order)
-            if (pl.init_bad[p] == 0)
-                for (int g = 0; g < pl.meta[p].B_pad / (128 * MIXED_CLUSTER); ++g) pl.items.push_back(WorkItem{p, g});
+            if (pl.init_bad[p] == 0) {
+                const int mode = pl.meta[p].N <= o.s1_max ? MODE_SINGLE : MODE_FULL;
+                for (int g = 0; g < pl.meta[p].B_pad / (128 * pl.cl); ++g) pl.items.push_back(WorkItem{p, g, mode});
+                if (mode == MODE_SINGLE) pl.n_single += pl.meta[p].B_pad / (128 * pl.cl);
+            }
         // label chunks in the same order
         pl.order = order;
         int64_t total = 0;
@@ -430,7 +470,7 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int c = 0; c < pl.nlc; ++c) {
             for (int k = pl.lc_pair[c]; k < pl.lc_pair[c + 1]; ++k) {
                 const int p = order[k];
-                if (pl.init_bad[p] == 0) it += pl.meta[p].B_pad / (128 * MIXED_CLUSTER);
+                if (pl.init_bad[p] == 0) it += pl.meta[p].B_pad / (128 * pl.cl);
             }
             pl.lc_item[c + 1] = it;
         }
@@ -449,7 +489,8 @@ struct Bufs {
     double *u;
     void *Z;
     unsigned int *colmax;
-    float *cpart;
+    unsigned long long *colL1;  // tensor-core path, BF16: column L1 bounds (units of 2^-40)
+    float *cpart, *cpart1;
     i128 *t_ex, *s1o;
     ColConst *cc;
     unsigned short *zq;
@@ -460,6 +501,8 @@ struct Bufs {
     PairOut *out;
     void *xy;
     WorkItem *items;
+    uint32_t *glist;   // BF16 tensor-core path: relabellings left by the single-slice pass
+    WorkItem *gitems;  // and the gathered pass's work list
     int *order;  // mixed path: pairs in the items' order
     float *lam;  // Ritz values [P][16] (features mode)
 };
@@ -481,8 +524,13 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
     b.Z = own_Z ? (void *)cv.take<char>((size_t)pl.total_rows_pad * d * esz) : nullptr;
     b.colmax = cv.take<unsigned int>((size_t)P * pl.o.d_pad);
     b.xy = xy_bytes ? (void *)cv.take<char>(xy_bytes) : nullptr;
+    const bool grid_slices = !align_only && pl.o.path == HB_PATH_MIXED && pl.o.dtype == HB_BF16;
+    b.colL1 = grid_slices ? cv.take<unsigned long long>((size_t)P * pl.o.d_pad) : nullptr;
+    b.glist = grid_slices && pl.n_single ? cv.take<uint32_t>((size_t)pl.total_gl) : nullptr;
+    b.gitems = grid_slices && pl.n_single ? cv.take<WorkItem>((size_t)(pl.total_gl / 128 + P)) : nullptr;
     if (!align_only) {
         b.cpart = cv.take<float>(nch * d);
+        b.cpart1 = cv.take<float>(nch * d);
         b.t_ex = cv.take<i128>((size_t)P * d);
         b.s1o = cv.take<i128>((size_t)P * d);
         b.cc = cv.take<ColConst>((size_t)P * pl.o.d_pad);
@@ -533,7 +581,9 @@ static void xrec(const Exec &ex, cudaEvent_t e)
 static float gemm_ms(const Plan &pl, const cudaEvent_t *gev)
 {
     float total = 0.f;
-    for (int c = 0; c < std::max(pl.nlc, 1); ++c) {
+    const int nl = std::max(pl.nlc, 1);
+    for (int c = 0; c <= nl; ++c) {
+        if (c == nl && pl.n_single == 0) break;  // the gathered pass runs only after a single-slice pass
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, gev[2 * c], gev[2 * c + 1]) == cudaSuccess) total += ms;
         else cudaGetLastError();  // not recorded: leave no sticky error for the next call
@@ -579,6 +629,7 @@ static int launch_count(const Plan &pl, unsigned int cap, int rgrid, bool host_i
         gemm = 0;
         for (int c = 0; c < pl.nlc; ++c) gemm += pl.lc_item[c + 1] > pl.lc_item[c] ? 1 : 0;
     }
+    if (mixed && pl.n_single) gemm += 2;  // the gathered pass: its work list and its GEMM
     return 7 * pieces + 1 + labels + gemm + 2 * (int)((cap + rgrid - 1) / rgrid);
 }
 
@@ -620,6 +671,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         CK(cudaEventRecord(ex.join, ex.side));
     }
     CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
+    if (b.colL1) CK(cudaMemsetAsync(b.colL1, 0, sizeof(unsigned long long) * P * o.d_pad, s));
     CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
     if (mixed && o.d_pad != d)
         CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
@@ -645,8 +697,8 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     } else if (xy_host) {
         CK(cudaMemcpyAsync(b.xy, xy_host, xy_bytes, cudaMemcpyHostToDevice, s));
     }
-    // lanes-along-tokens slices: tensor-core path, two BF16 slices, 16-byte rows
-    const bool tok_layout = mixed && o.slices == 2 && d % 8 == 0;
+    // lanes-along-tokens slices: tensor-core path, BF16 grid slices, 16-byte rows
+    const bool tok_layout = mixed && o.dtype == HB_BF16 && d % 8 == 0;
     const int64_t zq_ld = pl.total_rows_pad;
     xmark(ex, 0);
     for (int k = 0; k < pieces; ++k) {
@@ -655,12 +707,12 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         // steps 1-3 (column maxima feed the slice scales and the exact-sum windows)
         launch_colsum(b.meta, b.chunks, sp, d, o.dtype, b.part, b.s, b.bad, s);
         launch_axis(b.meta, sp, o, b.s, b.bad, b.st, b.u, s);
-        launch_reflect(b.meta, b.chunks, sp, o, b.st, b.u, Z, b.colmax, s);
+        launch_reflect(b.meta, b.chunks, sp, o, b.st, b.u, Z, b.colmax, features ? nullptr : b.colL1, s);
         CK(cudaGetLastError());
         // step 4: Z statistics, fixed-point slices, T_obs
         if (pieces == 1) xmark(ex, 1);
-        launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.part, b.cpart, b.zq, zq_ld, b.t_ex, b.s1o, b.cc,
-                      tok_layout, s);
+        launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.colL1, b.part, b.cpart, b.cpart1, b.zq, zq_ld,
+                      b.t_ex, b.s1o, b.cc, tok_layout, s);
         launch_tobs(b.meta, sp, o, b.t_ex, b.s1o, b.cc, b.st, s);
         CK(cudaGetLastError());
     }
@@ -688,14 +740,19 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
             ma.zq = b.zq;
             ma.zq_ld = zq_ld;
             ma.zq_rows = (int64_t)o.slices * o.d_pad;
+            ma.n_work_dev = nullptr;
+            ma.glist = b.glist;
             ma.list = b.list;
             ma.n_items = b.counters;
             ma.cap = cap;
             ma.overflow = b.counters + 1;
             ma.timeout = b.counters + 2;
             ma.T_out = T_out;
+            ma.wait_ns = pl.k.wait_ns;
+            ma.withhold = pl.k.withhold;
             ma.sms = ex.sms;
-            for (int c = 0; c < std::max(pl.nlc, 1); ++c) {
+            const int nl = std::max(pl.nlc, 1);
+            for (int c = 0; c < nl; ++c) {
                 if (c > 0) CK(cudaStreamWaitEvent(s, ex.lab_ev[c], 0));
                 ma.items = b.items + (pl.nlc ? pl.lc_item[c] : 0);
                 ma.n_work = pl.nlc ? pl.lc_item[c + 1] - pl.lc_item[c] : (int)pl.items.size();
@@ -703,6 +760,25 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
                 if (ex.gev) xrec(ex, ex.gev[2 * c]);
                 const cudaError_t e = launch_mixed(ma, s, err);
                 if (ex.gev) xrec(ex, ex.gev[2 * c + 1]);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
+                                "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
+                }
+            }
+            if (pl.n_single) {
+                // the gathered pass: every slice for the relabellings the single-slice pass
+                // left inside its band, in single CTAs (128 listed relabellings per item)
+                launch_gather_items(b.st, P, b.gitems, b.counters + 3, s);
+                ma.o.cg = 1;
+                ma.withhold = 0;
+                ma.items = b.gitems;
+                ma.n_work = -1;
+                ma.n_work_dev = b.counters + 3;
+                std::string err;
+                if (ex.gev) xrec(ex, ex.gev[2 * nl]);
+                const cudaError_t e = launch_mixed(ma, s, err);
+                if (ex.gev) xrec(ex, ex.gev[2 * nl + 1]);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
                     return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
@@ -800,7 +876,7 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             mark(c, 0, s);
             launch_colsum(b.meta, b.chunks, all, d, o.dtype, b.part, b.s, b.bad, s);
             launch_axis(b.meta, all, o, b.s, b.bad, b.st, b.u, s);
-            launch_reflect(b.meta, b.chunks, all, o, b.st, b.u, Z, nullptr, s);
+            launch_reflect(b.meta, b.chunks, all, o, b.st, b.u, Z, nullptr, nullptr, s);
             CK(cudaGetLastError());
             if (u_out) CK(cudaMemcpyAsync(u_out, b.u, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
             if (skipped_out) {
@@ -860,6 +936,7 @@ static hb_status run(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_bytes, 
     CK(cudaStreamWaitEvent(c->main, c->enter, 0));
     const hb_status hs = run_on(c, pl, xy_host, xy_bytes, xy_row_off, align_only, Z_out, u_out, skipped_out, T_out,
                                 c->main, out, tri);
+    if (!align_only && pl.o.path == HB_PATH_MIXED) c->withhold = 0;  // the test hook acts on one call
     CK(cudaEventRecord(c->leave, c->main));
     CK(cudaStreamWaitEvent(user, c->leave, 0));
     return hs;
@@ -937,7 +1014,7 @@ extern "C" hb_status hb_perm_test(hb_ctx *c, const void *X, int64_t n, const voi
     hb_opts op = *opts;
     if (op.path == HB_PATH_AUTO) op.path = route_for(c, n + m);
     Plan pl;
-    hs = make_plan(pl, 1, &n, &m, d, dtype, op, false, T_out != nullptr);
+    hs = make_plan(pl, 1, &n, &m, d, dtype, op, false, T_out != nullptr, ctx_opts(c));
     if (hs != HB_OK) return hs;
     pl.meta[0].X = X;
     pl.meta[0].Y = Y;
@@ -989,7 +1066,7 @@ static hb_status batched_routes(hb_ctx *c, int64_t P, const void *XY, const int6
         }
         op.path = r;
         Plan pl;
-        hs = make_plan(pl, S, ns.data(), ms.data(), d, dtype, op, false, false);
+        hs = make_plan(pl, S, ns.data(), ms.data(), d, dtype, op, false, false, ctx_opts(c));
         if (hs != HB_OK) break;
         for (int64_t i = 0; i < S; ++i) {
             pl.meta[i].X = base + (size_t)off[ix[i]] * d * esz;
@@ -1038,7 +1115,7 @@ extern "C" hb_status hb_perm_test_batched(hb_ctx *c, int64_t P, const void *XY, 
         op.path = only;
     }
     Plan pl;
-    hs = make_plan(pl, P, n, m, d, dtype, op, false, false);
+    hs = make_plan(pl, P, n, m, d, dtype, op, false, false, ctx_opts(c));
     if (hs != HB_OK) return hs;
     const size_t esz = dtype == HB_F32 ? 4 : 2;
     std::vector<int64_t> off(P + 1, 0);
@@ -1088,7 +1165,7 @@ struct hb_plan {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t lab_ev[LABEL_CHUNKS] = {};
     cudaEvent_t tev[7] = {};
-    cudaEvent_t gev[2 * LABEL_CHUNKS] = {};
+    cudaEvent_t gev[2 * (LABEL_CHUNKS + 1)] = {};
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1163,8 +1240,9 @@ extern "C" hb_status hb_plan_layout(int64_t P, const int64_t *n, const int64_t *
         }
     if (items && counts->n_items)
         for (size_t k = 0; k < pl.items.size(); ++k) {
-            items[2 * k] = pl.items[k].pair;
-            items[2 * k + 1] = pl.items[k].tile;
+            items[3 * k] = pl.items[k].pair;
+            items[3 * k + 1] = pl.items[k].tile;
+            items[3 * k + 2] = pl.items[k].mode;
         }
     // the pair order exists on every tensor-core path, also when no pair has work items
     if (order && pl.o.path == HB_PATH_MIXED)
@@ -1177,7 +1255,9 @@ static hb_status plan_build(hb_plan *q, int64_t P)
 {
     hb_ctx *c = q->c;
     Plan &pl = q->pl;
-    hb_status hs = make_plan(pl, P, q->n.data(), q->m.data(), q->d, q->dtype, q->opts, false, false);
+    CtxOpts k = ctx_opts(c);
+    k.withhold = 0;  // a graph replays every call: the one-call test hook does not apply
+    hb_status hs = make_plan(pl, P, q->n.data(), q->m.data(), q->d, q->dtype, q->opts, false, false, k);
     if (hs != HB_OK) return hs;
     const bool mixed = pl.o.path == HB_PATH_MIXED;
     q->esz = q->dtype == HB_F32 ? 4 : 2;
@@ -1463,6 +1543,29 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
     return HB_OK;
 }
 
+extern "C" hb_status hb_ctx_set_option(hb_ctx *c, int32_t option, int64_t value)
+{
+    if (!c) return fail(HB_ERR_INVALID_ARG, "ctx is NULL");
+    switch (option) {
+    case HB_OPT_WAIT_LIMIT_NS:
+        if (value < 1000 || value > 60000000000ll)
+            return fail(HB_ERR_INVALID_ARG, "wait limit %lld ns outside [1 us, 60 s]", (long long)value);
+        c->wait_ns = (uint64_t)value;
+        break;
+    case HB_OPT_SINGLE_SLICE_MAX_N:
+        if (value < 0 || value > 65536) return fail(HB_ERR_INVALID_ARG, "single-slice limit %lld", (long long)value);
+        c->s1_max = (int32_t)value;
+        break;
+    case HB_OPT_TEST_WITHHOLD_ARRIVAL:
+        c->withhold = value != 0;
+        break;
+    default:
+        return fail(HB_ERR_INVALID_ARG, "option %d unknown", option);
+    }
+    g_err.clear();
+    return HB_OK;
+}
+
 void hb_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
 
 // ---------------------------------------------------------------------------
@@ -1488,7 +1591,7 @@ static hb_status batched_common(hb_ctx *c, int64_t P, const void *XY, const int6
         op.exhaustive = 0;
     }
     Plan pl;
-    hs = make_plan(pl, P, n, m, d, dtype, op, false, T_out != nullptr);
+    hs = make_plan(pl, P, n, m, d, dtype, op, false, T_out != nullptr, ctx_opts(c));
     if (hs != HB_OK) return hs;
     const size_t esz = dtype == HB_F32 ? 4 : 2;
     int64_t off = 0;

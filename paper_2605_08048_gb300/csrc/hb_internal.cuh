@@ -24,9 +24,10 @@ struct PairMeta {
     int64_t lab_off;    // first word of this pair's label block [W][B_pad]
     int64_t B;          // relabellings (C(N, n) when exhaustive)
     int64_t T_off;      // offset of this pair's T_b values in T_out, -1 = none
+    int64_t g_off;      // tensor-core path: first entry of this pair's list of relabellings (B_pad entries)
     int32_t n, m, N, N_pad;
     int32_t W;          // 32-bit label words per relabelling
-    int32_t B_pad;      // B rounded up to 128
+    int32_t B_pad;      // B rounded up to the relabellings of a work item
     int32_t chunk0;     // first row chunk of this pair (X side then Y side)
     int32_t nchunk_x;   // row chunks of the X side
     int32_t nchunk_y;   // row chunks of the Y side
@@ -49,19 +50,21 @@ struct PairState {
     double A1o, A2o, To;     // observed per-group values and T_obs (FP64, exact path)
     double rx, ry;
     float tnorm;             // ||t|| (FP32) for the error band
-    float sumc2;             // sum_j c_j^2 of the per-column band constants
+    float sumc2;             // sum_j c_j^2 of the per-column band constants (all slices)
     unsigned long long count;
     unsigned long long rechecked;
     unsigned int band_max_bits;  // float bits of the largest band (atomicMax)
+    float sumc2_1;           // sum_j c1_j^2 (tensor-core path, BF16: the single-slice pass)
+    unsigned int n_gather;   // relabellings the single-slice pass left to the two-slice pass
     int32_t pad_;
 };
 
 // Per-column constants of one pair for the fast paths.
 struct ColConst {
-    float q_hi;   // fixed-point scale of the hi slice (mixed path); 0.5 for plain
+    float q_hi;   // scale of the first slice: 2^(E-8) (FP32 storage); 1 (BF16: slices hold values); 0.5 plain
     float t;      // column total of Z, rounded to FP32
-    float c;      // band constant: residual sum R_j (mixed) or gamma_K * sum|z| (plain)
-    float pad_;
+    float c;      // band constant: residual sum of all slices (tensor cores) or gamma_K * sum|z| (plain)
+    float c1;     // BF16 tensor-core path: residual sum of the first slice alone
 };
 
 // Shared launch options (flattened hb_opts).
@@ -71,8 +74,10 @@ struct RunOpts {
     int32_t stat, alt, align, reflect_side, exhaustive, path;
     int32_t d, d_pad, dtype, slices;
     int32_t want_T;
-    int32_t cw;      // z-columns per tensor-core column tile (128 for 2 slices, 64 for 3; half when narrow)
+    int32_t cw;      // z-columns per tensor-core tile of all slices (128 BF16, 64 FP32; half when narrow)
     int32_t cg;      // tensor-core path: 1 = one CTA per MMA, 2 = CTA pairs (M = 256)
+    int32_t nacc;    // accumulator columns of a tensor-core tile: slices * cw
+    int32_t s1_max;  // BF16 tensor-core path: pairs with N <= s1_max take the single-slice pass first
 };
 
 // ---------------------------------------------------------------------------
@@ -171,6 +176,59 @@ __device__ __forceinline__ int col_bound_exp(unsigned int maxbits)
 {
     if (maxbits == 0u) return -200;
     return (int)((maxbits >> 23) & 0xffu) - 126;
+}
+
+// ---------------------------------------------------------------------------
+// BF16 storage, tensor-core path: the two slices of one column of one pair.
+// Both are grids of powers of two that keep every FP32 accumulator of the
+// group-sum GEMM exact.  With L1 >= sum_i |z_i| over the pair's N tokens and
+// g = 2^eg, eg = ceil(log2 L1) - 23, the first slice k_i g = z_i rounded to
+// the grid g satisfies sum_i |k_i g| < L1 + N g/2 < 2^24 g, so every partial
+// sum of any subset is a multiple of g below 2^24 g: an exact FP32 value.  A
+// BF16 z_i whose last bit is >= g is its own first slice; smaller ones round
+// to a multiple of g of at most 8 significant bits, so the first slice is a
+// BF16 value too.  The second slice k2_i g2 = (z_i - k_i g) rounded to
+// g2 = g 2^(ceil(log2 N) - 23) has the same property (the residuals of the
+// first slice sum to at most N g/2 <= 2^22 g2) and at most 8 significant bits.
+// What both leave out, z_i - k_i g - k2_i g2, is nonzero only for values below
+// 2^7 g2 with bits under g2, and enters the error band.  Values below 2^-64
+// count as 0 (the oracle's rule) and are flushed before the split.
+// ---------------------------------------------------------------------------
+struct L1Grid {
+    int eg, eg2;   // exponents of g and g2
+    bool split;    // false: both slices 0 and the residual is the value
+    float g, inv_g, g2, inv_g2;
+};
+
+// l1fx = ceil(L1 * 2^40) (0: every value of the column is 0); N = tokens of the pair
+__device__ __forceinline__ L1Grid l1_grid(unsigned long long l1fx, int N)
+{
+    L1Grid G;
+    const int cl = l1fx <= 1ull ? 0 : 64 - __clzll((long long)(l1fx - 1ull));  // ceil(log2 l1fx)
+    const int cn = N <= 1 ? 0 : 32 - __clz(N - 1);                               // ceil(log2 N)
+    G.eg = cl - 40 - 23;
+    G.eg2 = G.eg + cn - 23;
+    // exact integer totals need g2 on the 2^-87 grid (g2 >= 2^-87, a normal float)
+    G.split = l1fx != 0ull && G.eg2 >= -87;
+    if (G.split) {
+        G.g = __int_as_float((G.eg + 127) << 23);
+        G.inv_g = __int_as_float((127 - G.eg) << 23);
+        G.g2 = __int_as_float((G.eg2 + 127) << 23);
+        G.inv_g2 = __int_as_float((127 - G.eg2) << 23);
+    } else {
+        G.g = G.inv_g = G.g2 = G.inv_g2 = 0.0f;
+    }
+    return G;
+}
+
+// The exact split z = k g + k2 g2 + r2 (r1 = z - k g); every step is exact in FP32.
+__device__ __forceinline__ void l1_split(float z, const L1Grid &G, float &k, float &k2, float &r1, float &r2)
+{
+    if (((__float_as_uint(z) >> 23) & 0xffu) < 63u) z = 0.0f;  // |z| < 2^-64 counts as 0
+    k = rintf(__fmul_rn(z, G.inv_g));
+    r1 = __fmaf_rn(-k, G.g, z);
+    k2 = rintf(__fmul_rn(r1, G.inv_g2));
+    r2 = __fmaf_rn(-k2, G.g2, r1);
 }
 
 __device__ __forceinline__ double pow2d(int e)  // 2^e for -1022 <= e <= 1023

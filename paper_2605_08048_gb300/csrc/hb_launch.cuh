@@ -22,11 +22,12 @@ void launch_colsum(const PairMeta *meta, const RowChunk *chunks, const PairSpan 
 void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *s, const int *bad,
                  PairState *pst, double *u, cudaStream_t st);
 void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
-                    const PairState *pst, const double *u, void *Z, unsigned int *colmax, cudaStream_t st);
+                    const PairState *pst, const double *u, void *Z, unsigned int *colmax,
+                    unsigned long long *colL1, cudaStream_t st);
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
-                   const PairState *pst, const void *Z, const unsigned int *colmax, i128 *tpart, float *cpart,
-                   unsigned short *zq, int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout,
-                   cudaStream_t st);
+                   const PairState *pst, const void *Z, const unsigned int *colmax,
+                   const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,
+                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout, cudaStream_t st);
 void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
                  const ColConst *cc, PairState *pst, cudaStream_t st);
 void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
@@ -43,13 +44,13 @@ void launch_recheck(unsigned int cap, unsigned int batch, int max_W, const PairM
 void launch_finalize(const PairMeta *meta, int P, const RunOpts &o, const PairState *pst, PairOut *out,
                      cudaStream_t st);
 // tensor-core path (hb_mixed.cu)
-// The tensor-core path runs clusters of MIXED_CLUSTER CTAs; the CTAs of a
-// cluster take consecutive 128-relabelling tiles of the same pair and share
-// every Z-slice tile through TMA multicast.
-constexpr int MIXED_CLUSTER = 4;
+// A work item is one 128-relabelling tile for single CTAs and two consecutive
+// tiles of one pair for CTA pairs (tcgen05 cta_group::2).
+enum : int32_t { MODE_FULL = 0, MODE_SINGLE = 1, MODE_GATHER = 2 };
 struct WorkItem {
     int32_t pair;
-    int32_t tile;  // group of MIXED_CLUSTER consecutive 128-relabelling tiles
+    int32_t tile;  // group of (cluster size) consecutive 128-row tiles of the pair's relabellings or list
+    int32_t mode;  // MODE_FULL, MODE_SINGLE (BF16: first slice only) or MODE_GATHER (listed relabellings)
 };
 struct MixedArgs {
     const PairMeta *meta;
@@ -62,15 +63,21 @@ struct MixedArgs {
     int64_t zq_ld;    // tokens per slice row
     int64_t zq_rows;  // slice rows
     const WorkItem *items;
-    int n_work;
+    int n_work;                      // >= 0: items; < 0: the count is *n_work_dev (written on the device)
+    const unsigned int *n_work_dev;
+    uint32_t *glist;                 // relabellings MODE_SINGLE leaves to MODE_GATHER (per pair from g_off)
     RecheckItem *list;
     unsigned int *n_items;
     unsigned int cap;
     unsigned int *overflow;
     unsigned int *timeout;
     float *T_out;
+    uint64_t wait_ns;                // wall-clock limit of every device barrier wait
+    int withhold;                    // test hook: one barrier arrival withheld (the wait runs out)
     int sms;
 };
+// the gathered pass's work list: ceil(n_gather / 128) items per pair, *n_items of them
+void launch_gather_items(const PairState *st, int P, WorkItem *items, unsigned int *n_items, cudaStream_t s);
 cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
 
 // learned triage (hb_triage.cu)

@@ -2,39 +2,53 @@
 // (Sec. 3.2, Eq. gemm: "a single GEMM call"), with the statistic, the error
 // band and the exceedance count fused into the epilogue (Algorithm 2).
 //
-// GEMM: D[b, c] = sum_i L[b, i] * Zs[i, c]
+// GEMM: D[b, a] = sum_i L[b, i] * Zs[i, a]
 //   A = labels L (128 relabellings x 64 tokens per stage), 0/1 in BF16,
 //       expanded from the packed label bits by the producer warps straight
 //       into the 128-byte-swizzled K-major shared-memory layout;
-//   B = the fixed-point slices of Z (hi, lo[, lo2] of `cw` columns, tokens
-//       contiguous), loaded by TMA with 128-byte swizzle;
-//   D = FP32 accumulators in TMEM, 128 lanes x (S*cw) columns, two buffers so
-//       the epilogue of one column tile overlaps the MMAs of the next.
-// Every slice value is an integer of magnitude <= 256 and every label is 0
-// or 1, so each FP32 accumulator holds an exact integer (|D| <= 256 * 65536 =
-// 2^24): the group sums are exact up to the residual of the slices, which the
-// error band carries as a per-column bound.
+//   B = slices of Z (tokens contiguous), loaded by TMA with 128-byte swizzle
+//       in boxes of up to 128 slice rows (one or two per stage for BF16);
+//   D = FP32 accumulators in TMEM, 128 lanes x nacc columns (nacc = slices x
+//       z-columns of the tile), two buffers so the epilogue of one column tile
+//       overlaps the MMAs of the next.
+// Every FP32 accumulator holds an exact sum: BF16 storage uses the grid
+// slices of l1_split (every partial sum is a multiple of the column's grid
+// below 2^24 grid units), FP32 storage three fixed-point slices of magnitude
+// <= 256 (|D| <= 256 * 65536 = 2^24).  The group sums are therefore exact up
+// to the residual of the slices used, which the error band carries as a
+// per-column bound.
+//
+// Work items (pair, tile group, mode):
+//   MODE_FULL   every slice (BF16: 2, FP32: 3), relabellings of the tiles;
+//               in-band relabellings go to the exact recheck;
+//   MODE_SINGLE BF16 only: the first grid slice alone (half the MMAs and
+//               half the B bytes); the band carries that slice's residual,
+//               and in-band relabellings are listed for MODE_GATHER;
+//   MODE_GATHER every slice, for the relabellings MODE_SINGLE listed (a
+//               tile's rows are gathered from the pair's list).
+// Each relabelling is decided once: by the single-slice pass when it falls
+// outside that pass's band, else by the two-slice pass, else exactly.
 //
 // Warp roles (448 threads, one CTA per SM, persistent over work items):
-//   warps 0-3  epilogue: TMEM -> registers, sigma_1 = sum_s q_s D_s,
-//              sigma_2 = t - sigma_1, squared norms, band, decision
+//   warps 0-3  epilogue: TMEM -> registers, sigma_1 = sum_s k_s D_s,
+//              sigma_2 = t - sigma_1, squared norms, band (its first-order
+//              term by Cauchy-Schwarz from the column bounds' norm), decision
 //   warp  4    TMA producer of the B tiles
 //   warp  5    MMA issuer (one elected lane); with CTA pairs (CG = 2) the odd
 //              CTA's warp 5 relays its A readiness to the even CTA instead
 //   warps 6-13 A producers (label bits -> BF16 0/1 tiles): warp 6 + i
 //              expands rows 32*(i%4) .. +31, tokens 32*(i/4) .. +31 (one
-//              label word) of every stage (with MX_APROD = 4, both words)
+//              label word) of every stage
 // The kernel is capped at 96 registers a thread (launch bound; the epilogue
 // reads 16 TMEM columns at a time), leaving room for the label draws, which
 // run beside it on another stream.
-// CG = 2 (HB_PATH_MIXED_2SM): the CTAs of each pair of the cluster (ranks 2k,
-// 2k+1) run tcgen05 cta_group::2 MMAs with M = 256; each holds its 128 rows of
-// A and half of the N columns of every B tile, so each SM receives half the B
-// bytes.  It is exact like the rest but not faster on GB300 at this tile
-// shape: shared-memory operand reads, not B ingress, bound both variants.
-// Every mbarrier wait is bounded (wall-clock limit); on expiry the kernel
-// raises the timeout flag, drains its own copies and MMAs, frees TMEM and
-// returns, and the host reports HB_ERR_TIMEOUT.
+// Variants: CG = 2 (tcgen05 cta_group::2 on CTA pairs, M = 256, each CTA
+// loading half of every B tile: the default route, half the B bytes per SM of
+// single CTAs) and CG = 1 (single CTAs, each loading its own B tiles; also the
+// gathered pass).  No copy is multicast.
+// Every mbarrier wait is bounded (wall-clock limit, a launch parameter); on
+// expiry the kernel raises the timeout flag, drains its own copies and MMAs,
+// frees TMEM and returns, and the host reports HB_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -47,12 +61,11 @@ namespace hb {
 
 constexpr int MX_M = 128;            // relabellings per tile (TMEM lanes)
 constexpr int MX_K = 64;             // tokens per stage (one 128-byte swizzle atom of BF16)
-constexpr int MX_NS = 4;             // pipeline stages
 constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
 constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB
-constexpr int MX_STAGE_BYTES = 48 * 1024;         // A + up to 256 B-rows x 128 B
-constexpr int MX_APROD = 8;         // A-producer warps (8: two per row block, one label word each; or 4)
-static_assert(MX_APROD == 8 || MX_APROD == 4, "four or eight A producers");
+constexpr int MX_NACC = 256;         // accumulator columns of one TMEM buffer
+constexpr int MX_BOXR_MIN = 32;      // slice rows per TMA box: at least this, at most 128
+constexpr int MX_APROD = 8;          // A-producer warps (two per row block, one label word each)
 constexpr int MX_THREADS = 192 + 32 * MX_APROD;
 // The launch bound names more threads than a CTA has, which caps the kernel at
 // 96 registers a thread (65536 / 576 rounded down): the SM then keeps about a
@@ -61,11 +74,11 @@ constexpr int MX_THREADS = 192 + 32 * MX_APROD;
 // launches.
 constexpr int MX_BOUND_THREADS = 576;
 static_assert(MX_BOUND_THREADS >= MX_THREADS, "launch bound");
-constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of 256 columns
-constexpr int MX_BAR_OFF = MX_NS * MX_STAGE_BYTES;
+constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of MX_NACC columns
+constexpr int MX_STAGE_AREA = 192 * 1024;  // CG = 1: 4 stages of 48 KB; CG = 2: 6 of 32 KB
+constexpr int MX_BAR_OFF = MX_STAGE_AREA;
 constexpr int MX_CONST_OFF = MX_BAR_OFF + 256;
-constexpr int MX_SMEM = 1024 + MX_CONST_OFF + 4 * 128 * 16;  // per-epilogue-warp column constants
-constexpr unsigned long long MX_WAIT_NS = 4000000000ull;  // 4 s per wait
+constexpr int MX_SMEM = 1024 + MX_CONST_OFF + 4 * MX_NACC * 8;  // per-epilogue-warp column constants
 
 struct MixedParams {
     const PairMeta *meta;
@@ -74,15 +87,21 @@ struct MixedParams {
     const ColConst *cc;
     const uint32_t *bits;
     const WorkItem *items;
-    int n_work;
+    int n_work;                      // items, or -1: read *n_work_dev
+    const unsigned int *n_work_dev;  // device item count (the gathered pass)
+    uint32_t *glist;                 // per pair (from g_off, B_pad entries): relabellings left by MODE_SINGLE
     RecheckItem *list;
     unsigned int *n_items;
     unsigned int cap;
     unsigned int *overflow;
     unsigned int *timeout;
     float *T_out;
+    uint64_t wait_ns;                // wall-clock limit of every barrier wait
+    int withhold;                    // test hook: CTA 0 withholds one A-stage arrival (the waits run out)
+    int box_rows;                    // slice rows of one TMA box (divides every tile's z-columns)
 };
 
+// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // PTX wrappers
 // ---------------------------------------------------------------------------
@@ -114,8 +133,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait for the phase with the given parity.  Returns false when the
-// wall-clock limit expired here or another thread already raised the flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int *timeout)
+// wall-clock limit (limit_ns) expired here or another thread already raised
+// the flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int *timeout, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -123,7 +143,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*(volatile unsigned int *)timeout) return false;
-            if (globaltimer() - t0 > MX_WAIT_NS) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicExch(timeout, 1u);
                 return false;
             }
@@ -146,7 +166,8 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
 }
 
 // bounded wait as mbar_wait, with cluster-scope acquire
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, unsigned int *timeout)
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, unsigned int *timeout,
+                                                  uint64_t limit_ns)
 {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -154,7 +175,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
         if (mbar_try_wait_cluster(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*(volatile unsigned int *)timeout) return false;
-            if (globaltimer() - t0 > MX_WAIT_NS) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicExch(timeout, 1u);
                 return false;
             }
@@ -206,16 +227,16 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
         : "memory");
 }
 
-// The same tile into the shared memory of every CTA in ctaMask (same offset),
-// completing bytes on each destination CTA's mbarrier at offset `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar,
-                                               uint16_t mask)
+// A whole warp waits for a barrier phase: lane 0 polls (one shared-memory
+// access per poll instead of 32) and the warp takes its outcome; __syncwarp
+// orders the other lanes' later accesses after lane 0's acquire.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, unsigned int *timeout, uint64_t limit_ns)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, timeout, limit_ns);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    __syncwarp();
+    return ok;
 }
 
 __device__ __forceinline__ uint32_t cluster_ctarank()
@@ -305,16 +326,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
                  : "memory");
 }
 
-// Arrives (once the prior MMAs complete) on the mbarrier at offset `bar` in
-// every CTA of ctaMask.
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     bar),
-                 "h"(mask)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile(
@@ -352,7 +363,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+__host__ __device__ __forceinline__ constexpr uint32_t idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -363,25 +374,49 @@ __device__ __forceinline__ uint32_t expand2(uint32_t b)
     return ((b & 1u) ? 0x3F80u : 0u) | ((b & 2u) ? 0x3F800000u : 0u);
 }
 
+// What every role of a CTA needs to know about one work item; every role
+// computes it the same way and skips the same items.
+struct ItemInfo {
+    int p;         // pair
+    int mode;      // MODE_FULL, MODE_SINGLE or MODE_GATHER
+    int S, cw, C;  // slices, z-columns per tile, column tiles
+    int KC;        // 64-token K chunks
+    int64_t row0;  // first relabelling (tiles) or list index (gathered) of this CTA's 128 rows
+    int64_t nrow;  // relabellings (tiles: B) or list length (gathered)
+    bool skip;
+};
+
+template <int DT>
+__device__ __forceinline__ ItemInfo item_info(const MixedParams &P, const WorkItem &w, int CL, int sub)
+{
+    ItemInfo I;
+    I.p = w.pair;
+    I.mode = w.mode;
+    const PairMeta &pm = P.meta[w.pair];
+    const PairState &st = P.st[w.pair];
+    I.S = w.mode == MODE_SINGLE ? 1 : (DT == DT_BF16 ? 2 : 3);
+    I.cw = P.o.nacc / I.S;
+    I.C = (P.o.d + I.cw - 1) / I.cw;
+    I.KC = pm.N_pad / MX_K;
+    I.row0 = ((int64_t)w.tile * CL + sub) * MX_M;
+    I.nrow = w.mode == MODE_GATHER ? (int64_t)st.n_gather : pm.B;
+    // uniform over the cluster: the item's first row decides
+    I.skip = st.status != ST_OK || (int64_t)w.tile * CL * MX_M >= I.nrow;
+    return I;
+}
+
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int S, int CW, int CG>
+template <int CG, int DT>
 __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
-    // CW z-columns per column tile: 128 (wide) or 64 (narrow) for two slices,
-    // 64 or 32 for three.  CG = 2: CTA pairs (ranks 2k, 2k+1) run M = 256 MMAs,
-    // each CTA holding NACC/2 rows of every B tile.
-    constexpr int NACC = S * CW;  // accumulator columns of one buffer
-    static_assert(NACC <= 256 && CW % 32 == 0 && NACC % 16 == 0, "column tile");
-    static_assert(CG == 1 || (CG == 2 && NACC % 16 == 0 && MIXED_CLUSTER % 2 == 0), "CTA pairs");
-    constexpr int BR = NACC / CG;                  // B rows of a stage in this CTA
-    constexpr uint32_t B_BYTES = (uint32_t)BR * 128u;
-    // stages: A (16 KB) + this CTA's B rows; CTA pairs hold half the B rows, so
-    // the same shared memory holds six stages instead of four
-    constexpr int STAGE = CG == 2 ? 32 * 1024 : MX_STAGE_BYTES;
-    constexpr int NS = CG == 2 ? 6 : MX_NS;
-    static_assert(NS * STAGE <= MX_BAR_OFF && MX_A_BYTES + (int)B_BYTES <= STAGE, "stage layout");
+    constexpr int CL = CG;  // CTAs per work item (a cluster of two for CTA pairs)
+    // stages: A (16 KB) + this CTA's B rows (up to 256 x 128 B; CTA pairs hold
+    // half, so the same shared memory holds six stages instead of four)
+    constexpr int STAGE = CG == 2 ? 32 * 1024 : 48 * 1024;
+    constexpr int NS = CG == 2 ? 6 : 4;
+    static_assert(NS * STAGE <= MX_STAGE_AREA, "stage layout");
     // CG = 2: the odd CTA reports its A stages to the even one in groups of RG
     // (a cluster-scope release costs about as much as a stage's MMAs, so one per
     // group rather than per stage); the even CTA waits at the first stage of each
@@ -393,8 +428,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = sbase + MX_BAR_OFF;
-    auto full_a = [&](int s) { return bar0 + 8u * s; };
-    auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
+    // full(s): the stage's A tile (one arrival per producer warp) and B tile (the TMA
+    // thread's expect_tx arrival and the copies' bytes) are in place; with CTA pairs
+    // the odd CTA's barrier counts its A tile only (its B half lands on the even CTA's)
+    auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
     auto acc_full = [&](int b) { return bar0 + 8u * (3 * NS + b); };
     auto acc_empty = [&](int b) { return bar0 + 8u * (3 * NS + 2 + b); };
@@ -406,19 +443,19 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RunOpts &o = P.o;
-    const int C = o.d_pad / CW;
-    // cluster: CTA `crank` of cluster `cid` owns tile (group * MIXED_CLUSTER + crank)
-    const uint32_t crank = cluster_ctarank();
-    const int cid = (int)blockIdx.x / MIXED_CLUSTER, ncl = (int)gridDim.x / MIXED_CLUSTER;
-    constexpr uint16_t CMASK = (uint16_t)((1u << MIXED_CLUSTER) - 1u);
+    const uint64_t lim = P.wait_ns;
+    const int nacc = o.nacc;
+    const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
+    const int cid = (int)blockIdx.x / CL, ncl = (int)gridDim.x / CL;
     const bool leader = CG == 1 || (crank & 1u) == 0u;  // issues the MMAs (CG = 2: the even CTA)
     const uint16_t pair_mask = (uint16_t)((CG == 2 ? 3u : 1u) << (crank & ~(uint32_t)(CG - 1)));
+    const int n_work = P.n_work >= 0 ? P.n_work : (int)*P.n_work_dev;
+    const int sub = (int)crank;  // this CTA's 128-row tile within the item's CL tiles
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(full_a(s), MX_APROD);
-            mbar_init(full_b(s), 1);
-            mbar_init(empty(s), CG == 2 ? 1 : MIXED_CLUSTER);  // CG = 2: the pair's commit; else one per CTA
+            mbar_init(full(s), MX_APROD + (leader ? 1 : 0));
+            mbar_init(empty(s), 1);  // the MMA commit (CG = 2: the pair's commit reaches both CTAs)
             mbar_init(peer_ready(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -432,9 +469,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         tmem_alloc<CG>(smem_u32(tmem_holder), MX_TMEM_COLS);
         tmem_relinquish<CG>();
     }
-    // every barrier of every CTA is initialised before any multicast copy or commit
+    // every barrier of both CTAs of a pair is initialised before any copy or commit reaches it
     tc_fence_before();
-    cluster_sync();
+    if (CL > 1) cluster_sync();
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
@@ -445,32 +483,46 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             uint32_t phase = 0;
             long long issued = 0;
             bool ok = true;
-            for (int it = cid; it < P.n_work && ok; it += ncl) {
-                const WorkItem w = P.items[it];
-                if (P.st[w.pair].status != ST_OK) continue;
-                const PairMeta &pm = P.meta[w.pair];
-                const int KC = pm.N_pad / MX_K;
-                for (int c = 0; c < C && ok; ++c) {
-                    for (int kc = 0; kc < KC; ++kc) {
-                        if (!mbar_wait(empty(stage), phase ^ 1u, P.timeout)) {
+            // this CTA's share of a tile's nacc rows: all (CG = 1) or one half, in boxes
+            // of box_rows slice rows (a box never straddles two slices)
+            const int r_begin = CG == 2 ? (int)(crank & 1u) * (nacc / 2) : 0, r_cnt = nacc / CG;
+            const int br = P.box_rows, nb = r_cnt / br;
+            for (int it = cid; it < n_work && ok; it += ncl) {
+                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                if (I.skip) continue;
+                const PairMeta &pm = P.meta[I.p];
+                // slice row of each box in column tile 0 (tile c adds c * cw)
+                int yb[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int a = r_begin + k * br;
+                    yb[k] = k < nb ? (a / I.cw) * o.d_pad + a % I.cw : 0;
+                }
+                for (int c = 0; c < I.C && ok; ++c) {
+                    for (int kc = 0; kc < I.KC; ++kc) {
+                        if (!mbar_wait(empty(stage), phase ^ 1u, P.timeout, lim)) {
                             ok = false;
                             break;
                         }
-                        // every CTA expects its rows of the tile; the cluster's first CTA (per
-                        // half, with CTA pairs) fetches them once from L2 and multicasts them
-                        // (the slot is free in every destination: `empty` counts one commit
-                        // from every MMA-issuing CTA)
+                        const int x = (int)(pm.z_row + kc * MX_K);
+                        const uint32_t bdst = sbase + stage * STAGE + MX_A_BYTES;
                         if (CG == 1) {
-                            mbar_arrive_expect_tx(full_b(stage), B_BYTES);
-                            if (crank == 0)
-                                tma_load_2d_mc(sbase + stage * STAGE + MX_A_BYTES, &tmap, (int)(pm.z_row + kc * MX_K),
-                                               c * NACC, full_b(stage), CMASK);
+                            mbar_arrive_expect_tx(full(stage), (uint32_t)r_cnt * 128u);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                if (k >= nb) break;
+                                tma_load_2d(bdst + (uint32_t)(k * br) * 128u, &tmap, x, yb[k] + c * I.cw, full(stage));
+                            }
                         } else {
                             // each CTA of the pair loads its half into its own shared memory and
                             // the even CTA's barrier counts both halves
-                            if (leader) mbar_arrive_expect_tx(full_b(stage), 2u * B_BYTES);
-                            tma_load_2d_pair(sbase + stage * STAGE + MX_A_BYTES, &tmap, (int)(pm.z_row + kc * MX_K),
-                                             c * NACC + (int)(crank & 1u) * BR, mapa_rank(full_b(stage), crank & ~1u));
+                            if (leader) mbar_arrive_expect_tx(full(stage), (uint32_t)nacc * 128u);
+                            const uint32_t bar = mapa_rank(full(stage), crank & ~1u);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                if (k >= nb) break;
+                                tma_load_2d_pair(bdst + (uint32_t)(k * br) * 128u, &tmap, x, yb[k] + c * I.cw, bar);
+                            }
                         }
                         ++issued;
                         if (++stage == NS) {
@@ -491,7 +543,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                     ph ^= 1u;
                 }
                 unsigned int dummy = 0;
-                mbar_wait(full_b(s), ph, ok ? P.timeout : &dummy);
+                mbar_wait(full(s), ph, ok ? P.timeout : &dummy, lim);
             }
         }
     } else if (warp == 5 && !leader) {
@@ -503,14 +555,12 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             uint32_t phase = 0;
             bool ok = true;
             int pending = -1;  // first stage of a group not reported yet
-            for (int it = cid; it < P.n_work && ok; it += ncl) {
-                const WorkItem w = P.items[it];
-                if (P.st[w.pair].status != ST_OK) continue;
-                const PairMeta &pm = P.meta[w.pair];
-                const int KC = pm.N_pad / MX_K;
-                for (int c = 0; c < C && ok; ++c) {
-                    for (int kc = 0; kc < KC; ++kc) {
-                        if (!mbar_wait(full_a(stage), phase, P.timeout)) {
+            for (int it = cid; it < n_work && ok; it += ncl) {
+                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                if (I.skip) continue;
+                for (int c = 0; c < I.C && ok; ++c) {
+                    for (int kc = 0; kc < I.KC; ++kc) {
+                        if (!mbar_wait(full(stage), phase, P.timeout, lim)) {
                             ok = false;
                             break;
                         }
@@ -532,46 +582,48 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(MX_M * CG, NACC);
+            const uint32_t idesc = idesc_bf16(MX_M * CG, nacc);
+            // shared-memory descriptors: the high word is the same for every operand,
+            // the low word holds the start address (16-byte units) and the leading
+            // byte offset; stage s starts at sbase + s * STAGE and K step k adds 32
+            // bytes, so each MMA's descriptors are two integer adds away
+            const uint32_t dhi = (uint32_t)(sw128_desc(sbase) >> 32);
+            const uint32_t alo0 = (uint32_t)sw128_desc(sbase);
+            constexpr uint32_t STEP = STAGE >> 4, BOFF = MX_A_BYTES >> 4;
             int stage = 0, abuf = 0;
-            uint32_t phase = 0, aphase = 0;
+            uint32_t phase = 0, aphase = 0, alo = alo0;
             bool ok = true;
-            for (int it = cid; it < P.n_work && ok; it += ncl) {
-                const WorkItem w = P.items[it];
-                if (P.st[w.pair].status != ST_OK) continue;
-                const PairMeta &pm = P.meta[w.pair];
-                const int KC = pm.N_pad / MX_K;
-                for (int c = 0; c < C && ok; ++c) {
-                    if (!mbar_wait(acc_empty(abuf), aphase ^ 1u, P.timeout)) {
+            for (int it = cid; it < n_work && ok; it += ncl) {
+                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                if (I.skip) continue;
+                for (int c = 0; c < I.C && ok; ++c) {
+                    if (!mbar_wait(acc_empty(abuf), aphase ^ 1u, P.timeout, lim)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dt = tmem + (uint32_t)abuf * 256u;
-                    for (int kc = 0; kc < KC; ++kc) {
-                        if (!mbar_wait(full_a(stage), phase, P.timeout) || !mbar_wait(full_b(stage), phase, P.timeout) ||
-                            (CG == 2 && stage % RG == 0 && !mbar_wait_cluster(peer_ready(stage), phase, P.timeout))) {
+                    const uint32_t dt = tmem + (uint32_t)abuf * MX_NACC;
+                    for (int kc = 0; kc < I.KC; ++kc) {
+                        if (!mbar_wait(full(stage), phase, P.timeout, lim) ||
+                            (CG == 2 && stage % RG == 0 && !mbar_wait_cluster(peer_ready(stage), phase, P.timeout, lim))) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a0 = sbase + stage * STAGE, b0 = a0 + MX_A_BYTES;
-                        if (CG == 2) {
 #pragma unroll
-                            for (int k = 0; k < MX_K / 16; ++k)
-                                umma_bf16_pair(dt, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
-                                               (kc | k) != 0 ? 1u : 0u);
-                            umma_commit_pair_mc(empty(stage), pair_mask);  // frees this slot in both CTAs
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < MX_K / 16; ++k)
-                                umma_bf16(dt, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
-                                          (kc | k) != 0 ? 1u : 0u);
-                            umma_commit_mc(empty(stage), CMASK);  // frees this slot in every CTA's view
+                        for (int k = 0; k < MX_K / 16; ++k) {
+                            const uint64_t ad = ((uint64_t)dhi << 32) | (alo + 2u * k);
+                            const uint64_t bd = ((uint64_t)dhi << 32) | (alo + BOFF + 2u * k);
+                            if (CG == 2) umma_bf16_pair(dt, ad, bd, idesc, (kc | k) != 0 ? 1u : 0u);
+                            else umma_bf16(dt, ad, bd, idesc, (kc | k) != 0 ? 1u : 0u);
                         }
+                        if (CG == 2) umma_commit_pair_mc(empty(stage), pair_mask);  // frees this slot in both CTAs
+                        else umma_commit(empty(stage));
+                        alo += STEP;
                         if (++stage == NS) {
                             stage = 0;
                             phase ^= 1u;
+                            alo = alo0;
                         }
                     }
                     if (!ok) break;
@@ -585,72 +637,71 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             if (CG == 2) umma_commit_pair_mc(drain, (uint16_t)(1u << crank));
             else umma_commit(drain);
             unsigned int dummy = 0;
-            mbar_wait(drain, 0, ok ? P.timeout : &dummy);
+            mbar_wait(drain, 0, ok ? P.timeout : &dummy, lim);
         }
     } else if (warp >= 6) {
         // ---------------- A producers: label bits -> BF16 0/1 ----------------
         const int pi = warp - 6;
         const int r = (pi & 3) * 32 + lane;  // relabelling row of the tile, 0..127
-        // with eight producers a warp fills one 32-token half of each stage, with
-        // four it fills both
-        constexpr int HALVES = 8 / MX_APROD;
-        const int half0 = MX_APROD == 8 ? (pi >> 2) : 0;
+        const int half = pi >> 2;            // the 32-token half of each stage this warp fills
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int it = cid; it < P.n_work && ok; it += ncl) {
-            const WorkItem w = P.items[it];
-            if (P.st[w.pair].status != ST_OK) continue;
-            const PairMeta &pm = P.meta[w.pair];
-            const int KC = pm.N_pad / MX_K;
-            const int tile = w.tile * MIXED_CLUSTER + (int)crank;
-            const uint32_t *lab = P.bits + pm.lab_off + (int64_t)tile * MX_M + r;
-            // this warp's label word of K-chunk kc and half h (identical for every column tile)
-            auto word = [&](int kc, int h) {
-                const int w0 = 2 * kc + half0 + h;
-                return w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
+        bool withheld = false;
+        for (int it = cid; it < n_work && ok; it += ncl) {
+            const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+            if (I.skip) continue;
+            const PairMeta &pm = P.meta[I.p];
+            // this row's relabelling: the tile's row, or the listed one (gathered pass)
+            const int64_t idx = I.row0 + r;
+            const bool valid = idx < I.nrow;
+            const int64_t b = !valid ? 0 : I.mode == MODE_GATHER ? (int64_t)P.glist[pm.g_off + idx] : idx;
+            const uint32_t *lab = P.bits + pm.lab_off + b;
+            // this warp's label word of K-chunk kc (identical for every column tile)
+            auto word = [&](int kc) {
+                const int w0 = 2 * kc + half;
+                return valid && w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
             };
             // loads run MX_PF stages ahead of the expansion (a register ring,
             // wrapping across column tiles), which covers the DRAM latency
-            uint32_t rw[HALVES][MX_PF];
+            uint32_t rw[MX_PF];
             int knext = 0;  // K-chunk of the next load
 #pragma unroll
             for (int i = 0; i < MX_PF; ++i) {
-#pragma unroll
-                for (int h = 0; h < HALVES; ++h) rw[h][i] = word(knext, h);
-                if (++knext == KC) knext = 0;
+                rw[i] = word(knext);
+                if (++knext == I.KC) knext = 0;
             }
-            for (int c = 0; c < C && ok; ++c) {
-                for (int kc = 0; kc < KC; ++kc) {
+            for (int c = 0; c < I.C && ok; ++c) {
+                for (int kc = 0; kc < I.KC; ++kc) {
                     // warp-uniform outcome, so the __syncwarp below is always complete
-                    if (!__all_sync(0xffffffffu, mbar_wait(empty(stage), phase ^ 1u, P.timeout))) {
+                    if (!warp_wait(empty(stage), phase ^ 1u, P.timeout, lim)) {
                         ok = false;
                         break;
                     }
                     uint8_t *row = smem + stage * STAGE + r * 128;
+                    const uint32_t wd = rw[0];
 #pragma unroll
-                    for (int h = 0; h < HALVES; ++h) {
-                        const uint32_t wd = rw[h][0];
+                    for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
+                    rw[MX_PF - 1] = word(knext);
 #pragma unroll
-                        for (int i = 0; i + 1 < MX_PF; ++i) rw[h][i] = rw[h][i + 1];
-                        rw[h][MX_PF - 1] = word(knext, h);
-                        const int half = half0 + h;
-#pragma unroll
-                        for (int cl = 0; cl < 4; ++cl) {
-                            const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
-                            const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
-                            uint4 v;
-                            v.x = expand2(b8);
-                            v.y = expand2(b8 >> 2);
-                            v.z = expand2(b8 >> 4);
-                            v.w = expand2(b8 >> 6);
-                            *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
-                        }
+                    for (int cl = 0; cl < 4; ++cl) {
+                        const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
+                        const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
+                        uint4 v;
+                        v.x = expand2(b8);
+                        v.y = expand2(b8 >> 2);
+                        v.z = expand2(b8 >> 4);
+                        v.w = expand2(b8 >> 6);
+                        *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
                     }
-                    if (++knext == KC) knext = 0;
+                    if (++knext == I.KC) knext = 0;
                     fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(full_a(stage));
+                    // test hook: CTA 0's first producer warp withholds its first arrival, so
+                    // the MMA thread's wait for that stage runs out
+                    const bool hold = P.withhold && !withheld && blockIdx.x == 0 && pi == 0;
+                    withheld |= hold;
+                    if (lane == 0 && !hold) mbar_arrive(full(stage));
                     if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
@@ -661,64 +712,104 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     } else {
         // ---------------- epilogue (warps 0-3 = TMEM lanes 0-127) ----------------
         const int r = threadIdx.x;  // TMEM lane = relabelling row
-        float4 *consts = (float4 *)(smem + MX_CONST_OFF) + warp * 128;
+        float2 *consts = (float2 *)(smem + MX_CONST_OFF) + warp * MX_NACC;
         int abuf = 0;
         uint32_t aphase = 0;
         bool ok = true;
-        // rounding chain of each squared norm: 8 FMAs per interleaved accumulator,
-        // 2 combining adds, 4 chunk adds per tile, then exact-enough FP64 across
-        // tiles and one final rounding to FP32
-        const float chain = 17.0f;
-        for (int it = cid; it < P.n_work && ok; it += ncl) {
-            const WorkItem w = P.items[it];
-            const int p = w.pair;
-            if (P.st[p].status != ST_OK) continue;
+        // rounding chain of each squared norm: 4 FMAs per interleaved accumulator,
+        // 2 combining adds, up to 16 chunk adds per tile, then exact-enough FP64
+        // across tiles and one final rounding to FP32
+        const float chain = 29.0f;
+        for (int it = cid; it < n_work && ok; it += ncl) {
+            const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+            if (I.skip) continue;
+            const int p = I.p;
             const PairMeta &pm = P.meta[p];
-            double Q1 = 0.0, Q2 = 0.0, E1 = 0.0, E2 = 0.0;
-            for (int c = 0; c < C; ++c) {
-                float tq1 = 0.f, tq2 = 0.f, te1 = 0.f, te2 = 0.f;
-                // this warp's copy of the tile's column constants (no cross-warp barrier)
+            const bool single = I.mode == MODE_SINGLE;
+            const int nch = I.cw / 16;
+            double Q1 = 0.0, Q2 = 0.0;
+            for (int c = 0; c < I.C; ++c) {
+                // this warp's copy of the tile's column constants (scale, total; no
+                // cross-warp barrier); columns past d hold zeros
                 __syncwarp();
-                for (int jj = lane; jj < CW; jj += 32) {
-                    const ColConst k = P.cc[(int64_t)p * o.d_pad + c * CW + jj];
-                    consts[jj] = make_float4(k.q_hi, k.t, k.c, 0.f);
+                for (int jj = lane; jj < I.cw; jj += 32) {
+                    const int j = c * I.cw + jj;
+                    float2 k = make_float2(0.f, 0.f);
+                    if (j < o.d) {
+                        const ColConst q = P.cc[(int64_t)p * o.d_pad + j];
+                        k = make_float2(q.q_hi, q.t);
+                    }
+                    consts[jj] = k;
                 }
                 __syncwarp();
-                if (!__all_sync(0xffffffffu, mbar_wait(acc_full(abuf), aphase, P.timeout))) {
+                if (!warp_wait(acc_full(abuf), aphase, P.timeout, lim)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)abuf * 256u;
-                // 16 accumulator columns per TMEM load keep the epilogue within the
-                // kernel's register budget (the label draws run beside the GEMM in
-                // the registers it leaves free)
-#pragma unroll 1
-                for (int ch = 0; ch < CW / 16; ++ch) {
-                    uint32_t dh[16], dl[16], dl2[16];
-                    tmem_ld16(tb + ch * 16, dh);
-                    tmem_ld16(tb + CW + ch * 16, dl);
-                    if (S == 3) tmem_ld16(tb + 2 * CW + ch * 16, dl2);
-                    tmem_ld_wait();
-                    float pq1[4] = {0.f, 0.f, 0.f, 0.f}, pq2[4] = {0.f, 0.f, 0.f, 0.f};
-                    float pe1[4] = {0.f, 0.f, 0.f, 0.f}, pe2[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float4 k = consts[ch * 16 + i];
-                        // sigma_1 = q_hi*D_hi + q_lo*D_lo (+ q_lo2*D_lo2): exact products, one rounding each
-                        float s1 = __fmul_rn(__uint_as_float(dh[i]), k.x);
-                        s1 = __fmaf_rn(__uint_as_float(dl[i]), k.x * (1.0f / 512.0f), s1);
-                        if (S == 3) s1 = __fmaf_rn(__uint_as_float(dl2[i]), k.x * (1.0f / 262144.0f), s1);
-                        const float s2 = k.y - s1;
-                        pq1[i & 3] = fmaf(s1, s1, pq1[i & 3]);
-                        pq2[i & 3] = fmaf(s2, s2, pq2[i & 3]);
-                        pe1[i & 3] = fmaf(fabsf(s1), k.z, pe1[i & 3]);
-                        pe2[i & 3] = fmaf(fabsf(s2), k.z, pe2[i & 3]);
-                    }
+                const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)abuf * MX_NACC;
+                float pq1[4] = {0.f, 0.f, 0.f, 0.f}, pq2[4] = {0.f, 0.f, 0.f, 0.f};
+                float tq1 = 0.f, tq2 = 0.f;
+                // per column: sigma_1, sigma_2 = t - sigma_1 and both squares; the band's
+                // first-order term comes from ||sigma_g|| ||c|| (Cauchy-Schwarz) below, so
+                // no per-column band work is needed
+                auto column = [&](int i, float s1, float t) {
+                    const float s2 = t - s1;
+                    pq1[i & 3] = fmaf(s1, s1, pq1[i & 3]);
+                    pq2[i & 3] = fmaf(s2, s2, pq2[i & 3]);
+                };
+                auto fold = [&]() {
                     tq1 += (pq1[0] + pq1[1]) + (pq1[2] + pq1[3]);
                     tq2 += (pq2[0] + pq2[1]) + (pq2[2] + pq2[3]);
-                    te1 += (pe1[0] + pe1[1]) + (pe1[2] + pe1[3]);
-                    te2 += (pe2[0] + pe2[1]) + (pe2[2] + pe2[3]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) pq1[q] = pq2[q] = 0.f;
+                };
+                if (DT == DT_BF16 && I.S == 1) {
+                    // the single-slice pass (the hot path): the slice holds values, so
+                    // sigma_1 = D exactly; the next chunk's TMEM load is in flight while
+                    // this one is consumed
+                    uint32_t da[16], db[16];
+                    tmem_ld16(tb, da);
+                    tmem_ld_wait();
+#pragma unroll 1
+                    for (int ch = 0; ch < nch; ch += 2) {
+                        tmem_ld16(tb + (ch + 1) * 16, db);  // nch is even
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) column(i, __uint_as_float(da[i]), consts[ch * 16 + i].y);
+                        fold();
+                        tmem_ld_wait();
+                        if (ch + 2 < nch) tmem_ld16(tb + (ch + 2) * 16, da);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) column(i, __uint_as_float(db[i]), consts[(ch + 1) * 16 + i].y);
+                        fold();
+                        tmem_ld_wait();
+                    }
+                } else {
+                    // every slice: sigma_1 = D_0 + D_1 (BF16 grid slices hold values; one
+                    // rounding) or q_hi (D_0 + D_1/2^9 + D_2/2^18) for the fixed-point slices
+                    // of FP32 storage (exact products, one rounding per added slice)
+#pragma unroll 1
+                    for (int ch = 0; ch < nch; ++ch) {
+                        uint32_t d0[16], d1[16], d2[16];
+                        tmem_ld16(tb + ch * 16, d0);
+                        tmem_ld16(tb + I.cw + ch * 16, d1);
+                        if (DT == DT_F32) tmem_ld16(tb + 2 * I.cw + ch * 16, d2);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float2 k = consts[ch * 16 + i];
+                            float s1;
+                            if (DT == DT_BF16) {
+                                s1 = __fadd_rn(__uint_as_float(d0[i]), __uint_as_float(d1[i]));
+                            } else {
+                                s1 = __fmul_rn(__uint_as_float(d0[i]), k.x);
+                                s1 = __fmaf_rn(__uint_as_float(d1[i]), k.x * (1.0f / 512.0f), s1);
+                                s1 = __fmaf_rn(__uint_as_float(d2[i]), k.x * (1.0f / 262144.0f), s1);
+                            }
+                            column(i, s1, k.y);
+                        }
+                        fold();
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -730,22 +821,29 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                 if (abuf == 0) aphase ^= 1u;
                 Q1 += (double)tq1;
                 Q2 += (double)tq2;
-                E1 += (double)te1;
-                E2 += (double)te2;
             }
             if (!ok) break;
-            const float q1 = (float)Q1, q2 = (float)Q2, e1 = (float)E1, e2 = (float)E2;
-            // decision for relabelling b of this tile
-            const int64_t b = (int64_t)(w.tile * MIXED_CLUSTER + (int)crank) * MX_M + r;
+            const float q1 = (float)Q1, q2 = (float)Q2;
+            // decision for this row's relabelling
+            const int64_t idx = I.row0 + r;
             int dec = -2;
             float T = 0.f, band = 0.f;
-            if (b < pm.B) {
+            if (idx < I.nrow) {
+                const int64_t b = I.mode == MODE_GATHER ? (int64_t)P.glist[pm.g_off + idx] : idx;
                 const PairState &s = P.st[p];
-                const float dq1 = q_bound(e1, q1, q1, q2, s.tnorm, s.sumc2, chain);
-                const float dq2 = q_bound(e2, q2, q1, q2, s.tnorm, s.sumc2, chain);
+                const float sc2 = single ? s.sumc2_1 : s.sumc2;
+                // sum_j |sigma_g,j| c_j <= ||sigma_g|| ||c||, with ||sigma_g||^2 <= q_g (1 + chain u)
+                const float ec = 1.0f + (chain + 4.0f) * U32;
+                const float e1 = __fmul_ru(__fsqrt_ru(__fmul_ru(q1, sc2)), ec);
+                const float e2 = __fmul_ru(__fsqrt_ru(__fmul_ru(q2, sc2)), ec);
+                const float dq1 = q_bound(e1, q1, q1, q2, s.tnorm, sc2, chain);
+                const float dq2 = q_bound(e2, q2, q1, q2, s.tnorm, sc2, chain);
                 dec = fast_decide(o.stat, o.alt, (float)o.d, (float)pm.n, (float)pm.m, q1, q2, dq1, dq2,
                                   (float)s.To, &T, &band);
-                if (dec < 0) push_recheck(P.list, P.n_items, P.cap, P.overflow, p, (uint32_t)b);
+                if (dec < 0) {
+                    if (single) P.glist[pm.g_off + atomicAdd(&P.st[p].n_gather, 1u)] = (uint32_t)b;
+                    else push_recheck(P.list, P.n_items, P.cap, P.overflow, p, (uint32_t)b);
+                }
                 if (P.T_out && pm.T_off >= 0) P.T_out[pm.T_off + b] = T;
             }
             const unsigned int ex = __ballot_sync(0xffffffffu, dec == 1);
@@ -759,14 +857,57 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         }
     }
 
-    // no CTA leaves while a peer may still multicast into its shared memory or
+    // no CTA leaves while a peer may still copy into its shared memory or
     // arrive on its barriers (every role above drained its own copies and MMAs)
     tc_fence_before();
-    cluster_sync();
+    if (CL > 1) cluster_sync();
+    else __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc<CG>(tmem, MX_TMEM_COLS);
     }
+}
+
+// ---------------------------------------------------------------------------
+// the gathered pass: one work item per 128 listed relabellings of a pair
+// ---------------------------------------------------------------------------
+// Single block: per pair the listed count n_gather, items in pair order.
+__global__ void k_gather_items(const PairState *__restrict__ st, int P, WorkItem *__restrict__ items,
+                               unsigned int *__restrict__ n_items)
+{
+    __shared__ unsigned int warp_tot[32];
+    __shared__ unsigned int base_s;
+    if (threadIdx.x == 0) base_s = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+    for (int p0 = 0; p0 < P; p0 += (int)blockDim.x) {
+        const int p = p0 + (int)threadIdx.x;
+        const unsigned int cnt = p < P && st[p].status == ST_OK ? (st[p].n_gather + MX_M - 1) / MX_M : 0u;
+        unsigned int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned int v = lane < nw ? warp_tot[lane] : 0u, w = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += t;
+            }
+            if (lane < nw) warp_tot[lane] = w - v;  // exclusive
+        }
+        __syncthreads();
+        const unsigned int at = base_s + warp_tot[wid] + incl - cnt;
+        for (unsigned int k = 0; k < cnt; ++k) items[at + k] = WorkItem{p, (int32_t)k, MODE_GATHER};
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base_s = at + cnt;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_items = base_s;
 }
 
 // ---------------------------------------------------------------------------
@@ -787,22 +928,37 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string &err)
     return fn;
 }
 
+typedef void (*MixedKernel)(const CUtensorMap, const MixedParams);
+
+template <int DT>
+static MixedKernel pick_kernel(int cg)
+{
+    return cg == 2 ? k_mixed<2, DT> : k_mixed<1, DT>;
+}
+
 cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
 {
     if (a.n_work == 0) return cudaSuccess;
-    const int S = a.o.slices;
-    if (S != 2 && S != 3) {
+    const int S = a.o.slices, nacc = a.o.nacc;
+    if (!((a.o.dtype == DT_BF16 && S == 2) || (a.o.dtype == DT_F32 && S == 3))) {
         err = "unsupported slice count";
         return cudaErrorInvalidValue;
     }
+    const int CGv = a.o.cg == 2 ? 2 : 1;
+    if (nacc > MX_NACC || nacc % (MX_BOXR_MIN * CGv) != 0 || nacc % S != 0 || (nacc / S) % MX_BOXR_MIN != 0) {
+        err = "unsupported column tile width";
+        return cudaErrorInvalidValue;
+    }
+    // the largest box that divides both a slice's z-columns of a tile and this
+    // CTA's share of the tile, at most 128 rows (at most 8 boxes per stage)
+    int br = 128;
+    while ((nacc / S) % br != 0 || (nacc / CGv) % br != 0) br >>= 1;
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode(err);
     if (!enc) return cudaErrorNotSupported;
-    const int CGv = a.o.cg == 2 ? 2 : 1;
-    const int nacc = S * a.o.cw / CGv;  // B rows of one CTA's share of a tile
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)a.zq_ld, (cuuint64_t)a.zq_rows};
     const cuuint64_t gstride[1] = {(cuuint64_t)a.zq_ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)MX_K, (cuuint32_t)nacc};
+    const cuuint32_t box[2] = {(cuuint32_t)MX_K, (cuuint32_t)br};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.zq, gdim, gstride, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -819,26 +975,25 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     prm.bits = a.bits;
     prm.items = a.items;
     prm.n_work = a.n_work;
+    prm.n_work_dev = a.n_work_dev;
+    prm.glist = a.glist;
     prm.list = a.list;
     prm.n_items = a.n_items;
     prm.cap = a.cap;
     prm.overflow = a.overflow;
     prm.timeout = a.timeout;
     prm.T_out = a.T_out;
-    void (*kern)(const CUtensorMap, const MixedParams) = nullptr;
-    if (CGv == 2) kern = S == 2 && a.o.cw == 128 ? k_mixed<2, 128, 2> : S == 3 && a.o.cw == 64 ? k_mixed<3, 64, 2> : nullptr;
-    else if (S == 2) kern = a.o.cw == 128 ? k_mixed<2, 128, 1> : a.o.cw == 64 ? k_mixed<2, 64, 1> : nullptr;
-    else kern = a.o.cw == 64 ? k_mixed<3, 64, 1> : a.o.cw == 32 ? k_mixed<3, 32, 1> : nullptr;
-    if (!kern) {
-        err = "unsupported column tile width";
-        return cudaErrorInvalidValue;
-    }
+    prm.wait_ns = a.wait_ns;
+    prm.withhold = a.withhold;
+    prm.box_rows = br;
+    const MixedKernel kern = a.o.dtype == DT_BF16 ? pick_kernel<DT_BF16>(CGv) : pick_kernel<DT_F32>(CGv);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
     if (e != cudaSuccess) return e;
+    const int CL = CGv;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = MIXED_CLUSTER;
+    attr[0].val.clusterDim.x = (unsigned)CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(MX_THREADS, 1, 1);
@@ -847,18 +1002,24 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // persistent: as many clusters as can be resident at once
-    cfg.gridDim = dim3(MIXED_CLUSTER * (unsigned)std::max(1, a.sms / MIXED_CLUSTER), 1, 1);
+    cfg.gridDim = dim3(CL * (unsigned)std::max(1, a.sms / CL), 1, 1);
     int max_clusters = 0;
     e = cudaOccupancyMaxActiveClusters(&max_clusters, (const void *)kern, &cfg);
     if (e != cudaSuccess || max_clusters < 1) {
         cudaGetLastError();
-        max_clusters = std::max(1, a.sms / MIXED_CLUSTER);
+        max_clusters = std::max(1, a.sms / CL);
     }
-    const int clusters = std::max(1, std::min(a.n_work, max_clusters));
-    cfg.gridDim = dim3((unsigned)(clusters * MIXED_CLUSTER), 1, 1);
+    // a device item count (n_work < 0) is not known here: launch every resident cluster
+    const int clusters = a.n_work > 0 ? std::max(1, std::min(a.n_work, max_clusters)) : max_clusters;
+    cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
     e = cudaLaunchKernelEx(&cfg, kern, map, prm);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+void launch_gather_items(const PairState *st, int P, WorkItem *items, unsigned int *n_items, cudaStream_t s)
+{
+    k_gather_items<<<1, 1024, 0, s>>>(st, P, items, n_items);
 }
 
 }  // namespace hb

@@ -356,7 +356,7 @@ def plan_layout(n, m, d: int, dtype, opts: hb_opts) -> dict:
     """hb_plan_layout: the launch layout of a batched call for these sizes
     (host computation, no GPU): row chunks [k][pair, side, row0, rows], input
     pieces [k][p0, p1, c0, c1], label/GEMM chunk cuts [k][order position, first
-    item], work items [k][pair, tile group] and the pair order, as int32
+    item], work items [k][pair, tile group, mode] and the pair order, as int32
     numpy arrays."""
     L = lib()
     vp = C.c_void_p
@@ -373,7 +373,7 @@ def plan_layout(n, m, d: int, dtype, opts: hb_opts) -> dict:
     _check(L.hb_plan_layout(*args, None, None, None, None, None))
     out = {"chunks": np.zeros((cnt.n_chunks, 4), np.int32), "pieces": np.zeros((cnt.n_pieces, 4), np.int32),
            "label_chunks": np.zeros((cnt.n_label_chunks + 1, 2), np.int32),
-           "items": np.zeros((cnt.n_items, 2), np.int32),
+           "items": np.zeros((cnt.n_items, 3), np.int32),
            "order": np.zeros(P if opts.path != HB_PATH_FP32_PLAIN else 0, np.int32)}
     _check(L.hb_plan_layout(*args, *(out[k].ctypes.data if out[k].size else None
                                      for k in ("chunks", "pieces", "label_chunks", "items", "order"))))
@@ -413,6 +413,17 @@ def declared_symbols(header: str | None = None):
     header = header or os.path.join(os.path.dirname(_HERE), "include", "hbperm.h")
     src = open(header).read()
     return sorted(set(re.findall(r"^\s*(?:hb_status|void|int64_t|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))
+
+
+HB_OPT_WAIT_LIMIT_NS, HB_OPT_SINGLE_SLICE_MAX_N, HB_OPT_TEST_WITHHOLD_ARRIVAL = 1, 2, 4
+
+
+def set_option(ctx: Context, option: int, value: int):
+    """hb_ctx_set_option: wait limit, single-slice pair limit, test hook."""
+    L = lib()
+    L.hb_ctx_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+    L.hb_ctx_set_option.restype = C.c_int
+    _check(L.hb_ctx_set_option(ctx.handle, int(option), int(value)))
 
 
 def set_timing(ctx: Context, enable: bool = True):

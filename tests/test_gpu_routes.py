@@ -35,8 +35,8 @@ def same_decision(a, b):
 
 
 def test_untuned_routes(ctx):
-    assert H.route(ctx, 2) == H.HB_PATH_MIXED
-    assert H.route(ctx, 65536) == H.HB_PATH_MIXED
+    assert H.route(ctx, 2) == H.HB_PATH_MIXED_2SM
+    assert H.route(ctx, 65536) == H.HB_PATH_MIXED_2SM
     assert H.route(ctx, 65537) == H.HB_PATH_FP32_PLAIN
     assert H.route(ctx, 1 << 20) == H.HB_PATH_FP32_PLAIN
     with pytest.raises(H.HbError):

@@ -9,7 +9,9 @@ import pytest
 
 from paper_2605_08048_gb300 import hbperm as H
 
-CHUNK_ROWS, CLUSTER_TILES, PIECES = 128, 4 * 128, 8
+CHUNK_ROWS, PIECES, S1_MAX = 128, 8, 8192
+# relabellings per work item: one 128-row tile for single CTAs, two for CTA pairs
+CLUSTER_TILES = {H.HB_PATH_MIXED: 128, H.HB_PATH_MIXED_NARROW: 128, H.HB_PATH_MIXED_2SM: 2 * 128}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -32,6 +34,7 @@ CASES = {
     "one_big": ([4000] + [30] * 20, [3000] + [25] * 20),
     "lognormal": lognormal_sizes(5, 300),
     "no_work": ([1, 5, 1], [9, 1, 1]),  # every pair has n < 2 or m < 2: no work items
+    "both_modes": ([5000, 30, 8000, 4096], [4000, 40, 200, 4096]),  # n + m above and at the single-slice limit
 }
 
 
@@ -40,11 +43,12 @@ def rup(x, k):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("path", [H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW, H.HB_PATH_FP32_PLAIN])
-def test_layout_invariants(case, path):
+@pytest.mark.parametrize("path", [H.HB_PATH_MIXED, H.HB_PATH_MIXED_NARROW, H.HB_PATH_MIXED_2SM, H.HB_PATH_FP32_PLAIN])
+@pytest.mark.parametrize("dtype", [H.HB_BF16, H.HB_F32])
+def test_layout_invariants(case, path, dtype):
     n, m = (np.asarray(v, dtype=np.int64) for v in CASES[case])
     P, B = len(n), 999
-    lay = H.plan_layout(n, m, 768, H.HB_BF16, H.make_opts(B=B, path=path))
+    lay = H.plan_layout(n, m, 768, dtype, H.make_opts(B=B, path=path))
     ch, pc = lay["chunks"], lay["pieces"]
 
     # row chunks: pair-major, X rows then Y rows, each side covered in order by
@@ -87,9 +91,12 @@ def test_layout_invariants(case, path):
     assert sorted(order) == list(range(P))
     key = [(-rup(N[p], 64), p) for p in order]
     assert key == sorted(key)
-    groups = rup(B, CLUSTER_TILES) // CLUSTER_TILES
+    tiles = CLUSTER_TILES[path]
+    groups = rup(B, tiles) // tiles
     valid = [p for p in order if n[p] >= 2 and m[p] >= 2]
-    want = [(p, g) for p in valid for g in range(groups)]
+    # BF16 pairs up to the single-slice limit run the single-slice pass (mode 1)
+    mode = {p: int(dtype == H.HB_BF16 and N[p] <= S1_MAX) for p in valid}
+    want = [(p, g, mode[p]) for p in valid for g in range(groups)]
     assert [tuple(x) for x in items] == want
     if not valid:
         assert len(items) == 0 and len(order) == P  # the order is written even with no work items
@@ -101,7 +108,7 @@ def test_layout_invariants(case, path):
     for c in range(len(lc) - 1):
         seg = [p for p in order[pos[c]:pos[c + 1]] if n[p] >= 2 and m[p] >= 2]
         assert it[c + 1] - it[c] == groups * len(seg)
-    words = np.array([((N[p] + 31) // 32) * rup(B, CLUSTER_TILES) for p in order])
+    words = np.array([((N[p] + 31) // 32) * rup(B, tiles) for p in order])
     if len(lc) > 2:
         assert words[:pos[1]].sum() >= words.sum() * 16 // 100 > words[:pos[1] - 1].sum()
 
