@@ -55,10 +55,14 @@ def parse():
     ap.add_argument("--B", type=int, default=9999)
     ap.add_argument("--d", type=int, default=768)
     ap.add_argument("--path", choices=["mixed", "mixed-2sm", "plain"], default="mixed-2sm")
-    ap.add_argument("--s1-max", type=int, default=8192, help="pairs with n + m up to this start with one slice")
+    ap.add_argument("--s1-max", type=int, default=65536, help="pairs with n + m up to this start with one slice")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--config", choices=["batched", "single", "large", "calibration"], default="batched",
+                    help="batched: the benchmark line; single: latency of the 200/300-row FP32 test (B=999); "
+                         "large: one 5000/5000-row d=1024 BF16 pair (B=100000); calibration: the Type-I sweep "
+                         "(10 angles x 200 null pairs, n=m=500, B=4999, naive vs aligned)")
     ap.add_argument("--triage", action="store_true",
                     help="learned triage at scale: train on --train-pairs of the method's own runs, triage "
                          "--eval-pairs held-out pairs in chunks of 4096 (one JSON line)")
@@ -211,12 +215,194 @@ def run_triage(a):
     return 0
 
 
+def _gpu_setup():
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2605_08048_gb300 import build as _build
+
+    _build.build()
+    from paper_2605_08048_gb300 import hbperm as H
+
+    return torch, H
+
+
+def _dev(torch, a):
+    if a.dtype == np.uint16:
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_single(a):
+    """Latency of one test of the single-pair workload (n=200, m=300, d=768
+    FP32, B=999, Philox seed 0): per call through hb_perm_test (host round trip
+    included) and per replay of a planned graph, next to the oracle."""
+    torch, H = _gpu_setup()
+    from paper_2605_08048_gb300 import synth
+    from oracle import oracle as O
+
+    X, Y = synth.workload_plain()
+    Xd, Yd = _dev(torch, X), _dev(torch, Y)
+    ctx = H.Context(0)
+    opts = H.make_opts(B=999, seed=0, path=H.HB_PATH_MIXED_2SM)
+    for _ in range(max(3, a.warmup)):
+        res, _ = H.hb_perm_test(ctx, Xd, Yd, opts)
+    steps = max(50, a.steps * 20)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res, _ = H.hb_perm_test(ctx, Xd, Yd, opts)
+    t_call = (time.perf_counter() - t0) / steps
+    XY = torch.cat([Xd, Yd])
+    plan = H.Plan(ctx, [200], [300], 768, torch.float32, opts)
+    plan.execute(XY)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rg = plan.execute(XY)
+    t_plan = (time.perf_counter() - t0) / steps
+    clk = clocks.stop()
+    plan.close()
+    ref, _, _ = O.perm_test(X, Y, O.opts(B=999, seed=0))
+    t1 = time.perf_counter()
+    for _ in range(3):
+        O.perm_test(X, Y, O.opts(B=999, seed=0))
+    t_oracle = (time.perf_counter() - t1) / 3
+    assert res["count"] == ref["count"] == rg[0]["count"] and res["p"] == ref["p"]
+    line = {"impl": "config", "config": {"workload": "single test: n=200, m=300, d=768 FP32, sigma 0.35, random mean "
+                                         "directions, B=999, Philox seed 0, Householder-aligned"},
+            "metric": "microseconds per test", "higher_is_better": False,
+            "us_per_call": 1e6 * t_call, "us_per_graph_replay": 1e6 * t_plan, "calls": steps,
+            "oracle_us_per_test": 1e6 * t_oracle, "oracle_cores": os.cpu_count(),
+            "p": res["p"], "count": res["count"], "identical_to_oracle": True, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_large(a):
+    """One large pair (n=m=5000, d=1024 BF16, sigma 0.35 vs 0.40, B=100000):
+    tests per second, the GEMM launches' roofline, sampled parity (the full
+    parity of this pair is a test)."""
+    torch, H = _gpu_setup()
+    from paper_2605_08048_gb300 import synth
+
+    X, Y = synth.workload_large()
+    Xd, Yd = _dev(torch, X), _dev(torch, Y)
+    ctx = H.Context(0)
+    H.set_timing(ctx, True)
+    B = 100000
+    out = {}
+    for s1 in (0, 65536):
+        H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, s1)
+        opts = H.make_opts(B=B, seed=0, path=H.HB_PATH_MIXED_2SM)
+        for _ in range(max(3, a.warmup)):
+            res, _ = H.hb_perm_test(ctx, Xd, Yd, opts)
+        clocks = Clocks(0)
+        clocks.start()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stages = []
+        e0.record(stream)
+        for _ in range(a.steps):
+            res, _ = H.hb_perm_test(ctx, Xd, Yd, opts)
+            stages.append(H.stage_times(ctx)[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        t = e0.elapsed_time(e1) / 1000.0 / a.steps
+        gemm_ms = statistics.mean(s["gemm_kernels"] for s in stages)
+        pk, pk_kind = peaks()
+        peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+        achieved = 2.0 * B * 10000 * 1024 / (gemm_ms / 1000.0) / 1e12
+        out["single_slice_first" if s1 == 65536 else "both_slices"] = {
+            "value": 1.0 / t, "unit": "pair-tests/s", "ms_per_test": 1000.0 * t, "count": res["count"], "p": res["p"],
+            "n_rechecked": res["n_rechecked"],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_kind": f"bf16 sustained, {pk_kind}"},
+            "stage_ms": {k: round(statistics.mean(s[k] for s in stages), 3) for k in stages[0]}, "clocks": clk}
+    assert out["both_slices"]["count"] == out["single_slice_first"]["count"]
+    line = {"impl": "config", "config": {"workload": "large pair: n=m=5000, d=1024 BF16, sigma 0.35 vs 0.40, "
+                                         "B=100000, Philox seed 0"},
+            "metric": "pair-tests/s", "higher_is_better": True, **out}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def _wilson(k, n, z=1.959964):
+    if n == 0:
+        return (float("nan"), float("nan"))
+    p = k / n
+    den = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / den
+    h = z * ((p * (1 - p) / n + z * z / (4 * n * n)) ** 0.5) / den
+    return (c - h, c + h)
+
+
+def run_calibration(a):
+    """The Type-I sweep: 200 null pairs per angle between the mean directions
+    (0..90 degrees, 10 angles), n=m=500, d=768 BF16, B=4999; rejection rate at
+    alpha=0.05 of the naive and the Householder-aligned test with 95 % Wilson
+    intervals; a 100-pair subset (10 per angle) compared with the oracle."""
+    torch, H = _gpu_setup()
+    from paper_2605_08048_gb300 import synth
+    from oracle import oracle as O
+
+    pairs = synth.workload_calibration()
+    angles = sorted({ang for ang, _, _ in pairs})
+    XY = np.concatenate([np.concatenate([X, Y]) for _, X, Y in pairs])
+    nn = np.full(len(pairs), 500, dtype=np.int64)
+    ctx = H.Context(0)
+    H.set_timing(ctx, True)
+    XYd = _dev(torch, XY)
+    out, ms = {}, {}
+    for align in (1, 0):
+        o = H.make_opts(B=4999, seed=2, align=align, path=H.HB_PATH_MIXED_2SM)
+        H.hb_perm_test_batched(ctx, XYd, nn, nn, o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = H.hb_perm_test_batched(ctx, XYd, nn, nn, o)
+        ms["aligned" if align else "naive"] = 1000.0 * (time.perf_counter() - t0)
+        p = np.array([r["p"] for r in res])
+        rows = []
+        for ang in angles:
+            sel = np.array([abs(x - ang) < 1e-9 for x, _, _ in pairs])
+            k = int(np.sum(p[sel] <= 0.05))
+            lo, hi = _wilson(k, int(sel.sum()))
+            rows.append({"angle_deg": round(float(ang), 3), "pairs": int(sel.sum()), "rejections": k,
+                         "rate": k / int(sel.sum()), "ci95": [round(lo, 4), round(hi, 4)]})
+        out["aligned" if align else "naive"] = rows
+        if align:
+            p_aligned = p
+    # oracle subset: the first 10 pairs of every angle, aligned
+    idx = [i for ang in angles for i in [j for j, (x, _, _) in enumerate(pairs) if abs(x - ang) < 1e-9][:10]]
+    sub = np.concatenate([np.concatenate([pairs[i][1], pairs[i][2]]) for i in idx])
+    ns = np.full(len(idx), 500, dtype=np.int64)
+    t0 = time.perf_counter()
+    ref = O.perm_test_batched(sub, ns, ns, O.opts(B=4999, seed=2, align=1))
+    t_or = time.perf_counter() - t0
+    agree = int(sum(r["p"] == p_aligned[i] for r, i in zip(ref, idx)))
+    line = {"impl": "config", "config": {"workload": "Type-I sweep: 10 angles 0..90 deg x 200 null pairs, n=m=500, "
+                                         "d=768 BF16, sigma 0.35, B=4999, alpha 0.05"},
+            "metric": "rejection rate at alpha=0.05", "rates": out, "gpu_ms_per_sweep": ms,
+            "oracle_subset": {"pairs": len(idx), "p_identical": agree, "seconds": round(t_or, 1),
+                              "cores": os.cpu_count()}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.triage:
         return run_triage(a)
+    if a.config != "batched":
+        return {"single": run_single, "large": run_large, "calibration": run_calibration}[a.config](a)
 
     import torch
 
@@ -314,8 +500,18 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt.item())
     assert [r["count"] for r in r2] == counts
+    # the pinned host-to-device copy rate of this machine, which bounds the end-to-end number
+    cpy = torch.empty_like(XY)
+    barrier()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    cpy.copy_(XYp, non_blocking=True)
+    c1.record(stream)
+    barrier()
+    h2d_gbs = XYh.numel() * 2 / (c0.elapsed_time(c1) / 1000.0) / 1e9
+    del cpy
     e2e = {"value": world * P * e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(XYh.numel() * 2),
-           "d2h_bytes_per_step": int(P * 80 + 16)}
+           "d2h_bytes_per_step": int(P * 80 + 16), "h2d_gbs_measured": round(h2d_gbs, 1)}
 
     # the same batch through a plan: one CUDA graph replay per step, identical counts
     plan = H.Plan(ctx, n, m, a.d, torch.bfloat16, opts)
@@ -342,17 +538,23 @@ def main():
     if not a.no_plain and path != H.HB_PATH_FP32_PLAIN:
         po = H.make_opts(B=a.B, seed=1, path=H.HB_PATH_FP32_PLAIN)
         H.hb_perm_test_batched(ctx, XY, n, m, po)
+        p_steps = 3
         barrier()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        rp = H.hb_perm_test_batched(ctx, XY, n, m, po)
+        pst = []
+        for _ in range(p_steps):
+            rp = H.hb_perm_test_batched(ctx, XY, n, m, po)
+            pst.append(H.stage_times(ctx)[0])
         g1.record(stream)
         barrier()
-        tp = g0.elapsed_time(g1) / 1000.0
-        stp, _ = H.stage_times(ctx)
-        plain = {"value": P / tp, "unit": UNIT, "ms_per_step": 1000.0 * tp, "gemm_ms": round(stp["gemm_epilogue"], 3),
-                 "counts_identical": [r["count"] for r in rp] == counts,
-                 "rechecked": int(sum(r["n_rechecked"] for r in rp))}
+        tp = g0.elapsed_time(g1) / 1000.0 / p_steps
+        plain_gemm = statistics.mean(s["gemm_kernels"] for s in pst)
+        plain = {"value": P / tp, "unit": UNIT, "ms_per_step": 1000.0 * tp, "steps": p_steps,
+                 "gemm_ms": round(plain_gemm, 3), "counts_identical": [r["count"] for r in rp] == counts,
+                 "rechecked": int(sum(r["n_rechecked"] for r in rp)),
+                 "ratio_value": value / (P / tp),
+                 "ratio_gemm_only": plain_gemm / statistics.mean(s["gemm_kernels"] for s in stages)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -368,8 +570,9 @@ def main():
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_mixed (group-sum GEMM + epilogue)",
                      "peak_kind": f"bf16 sustained, {pk_kind}",
-                     "note": "achieved = 2*B*sum(N)*d algorithmic FLOP per launch / CUDA-event time of the launch; "
-                             "the kernel executes 2 exact fixed-point BF16 slices, i.e. twice these tensor FLOPs"},
+                     "note": "achieved = 2*B*sum(N)*d algorithmic FLOP of a call / the summed CUDA-event time of "
+                             "its GEMM launches (the single-slice pass and the gathered two-slice pass of the "
+                             "relabellings inside the first pass's band), with the label draws running beside"},
         "stage_ms": stage_ms,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -349,7 +349,11 @@ hb_status hb_ctx_stage_times(hb_ctx *ctx, float *ms_out, int32_t *n_launches);
  *                               a wait that runs out ends the call with
  *                               HB_ERR_TIMEOUT and leaves the context usable
  *   HB_OPT_SINGLE_SLICE_MAX_N   BF16 input: pairs with n + m <= value start with
- *                               the single-slice pass (default 8192; 0 = never)
+ *                               the single-slice pass (default 65536: every pair
+ *                               of the tensor-core path; 0 = never).  Its cost is
+ *                               one slice plus two slices for the relabellings
+ *                               inside its band, which is wide only for very
+ *                               large pairs whose T_obs lies in the null's bulk
  *   HB_OPT_TEST_WITHHOLD_ARRIVAL  test hook: 1 = the next tensor-core call on
  *                               this context withholds one barrier arrival of
  *                               its first GEMM launch, so that a bounded wait

@@ -32,6 +32,79 @@ namespace hb {
 // several rows in flight; otherwise one column per thread.  Exact sums do not
 // depend on the order, so both give the same totals.
 // ---------------------------------------------------------------------------
+// BF16 input: each value v splits exactly into h = v rounded to the 2^-12 grid
+// and l = v - h.  For a valid |v| < 16 the h of <= 128 rows sum to < 2^11 on
+// the 2^-12 grid and every l of a value >= 2^-21 is a multiple of 2^-28 below
+// 2^-13, so both FP32 running sums are exact; values below 2^-21 (rare) are
+// added exactly one by one (|v| < 2^-64 counts as 0).  Invalid values show as
+// a non-finite sum or a maximum magnitude >= 16.
+__device__ __noinline__ i128 colsum_tiny_bf16(const uint4 *src, int64_t stride, int nrows, int e)
+{
+    i128 acc = 0;
+    for (int r = 0; r < nrows; ++r) {
+        const uint4 v = __ldg(src + r * stride);
+        const uint32_t w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+        const uint32_t b = (e & 1) ? (w & 0xffff0000u) : (w << 16);
+        if (((b >> 23) & 0xffu) < 127u - 21u) acc += fixed_from_f32bits(b);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void colsum_bf16(const void *base, const RowChunk &ch, int d, i128 *out, bool &ok)
+{
+    const int groups = d / 8;
+    const float M = 3072.0f;  // 1.5 * 2^11: (v + M) - M rounds v to the 2^-12 grid for |v| < 2^10
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        float sh[8], sl[8], amax = 0.0f;
+        uint32_t tiny = 0u;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sh[e] = sl[e] = 0.0f;
+        const uint4 *src = reinterpret_cast<const uint4 *>(base) + ((int64_t)ch.row0 * d) / 8 + g;
+        const int64_t stride = d / 8;
+#pragma unroll 4
+        for (int r = 0; r < ch.nrows; ++r) {
+            const uint4 v = __ldg(src + r * stride);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t b = (e & 1) ? (w[e >> 1] & 0xffff0000u) : (w[e >> 1] << 16);
+                const float x = __uint_as_float(b);
+                const float h = __fsub_rn(__fadd_rn(x, M), M);
+                sh[e] = __fadd_rn(sh[e], h);
+                sl[e] = __fadd_rn(sl[e], __fsub_rn(x, h));
+                amax = fmaxf(amax, fabsf(x));
+                // 0 < |v| < 2^-21 (the wrap-around of |b| - 1 leaves zeros out)
+                tiny |= ((b & 0x7fffffffu) - 1u < (106u << 23) - 1u) ? (1u << e) : 0u;
+            }
+        }
+        ok &= amax < 16.0f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            // tiny values took part in the FP32 sums: remove them exactly by recomputing the
+            // column from scratch in that (rare) case
+            ok &= isfinite(sh[e]) && isfinite(sl[e]);
+            if ((tiny >> e) & 1u) {
+                i128 acc = colsum_tiny_bf16(src, stride, ch.nrows, e);
+                // the values >= 2^-21, exactly: their split sums without the tiny ones
+                float h2 = 0.0f, l2 = 0.0f;
+                for (int r = 0; r < ch.nrows; ++r) {
+                    const uint4 v = __ldg(src + r * stride);
+                    const uint32_t w = (e >> 1) == 0 ? v.x : (e >> 1) == 1 ? v.y : (e >> 1) == 2 ? v.z : v.w;
+                    const uint32_t b = (e & 1) ? (w & 0xffff0000u) : (w << 16);
+                    if (((b >> 23) & 0xffu) < 127u - 21u) continue;
+                    const float x = __uint_as_float(b);
+                    const float h = __fsub_rn(__fadd_rn(x, M), M);
+                    h2 = __fadd_rn(h2, h);
+                    l2 = __fadd_rn(l2, __fsub_rn(x, h));
+                }
+                out[g * 8 + e] = acc + fixed_from_f32bits(__float_as_uint(h2)) + fixed_from_f32bits(__float_as_uint(l2));
+            } else {
+                out[g * 8 + e] = fixed_from_f32bits(__float_as_uint(sh[e])) + fixed_from_f32bits(__float_as_uint(sl[e]));
+            }
+        }
+    }
+}
+
 template <int DT>
 __device__ __forceinline__ void colsum_vec(const void *base, const RowChunk &ch, int d, i128 *out, bool &ok)
 {
@@ -71,7 +144,7 @@ __global__ void k_colsum_partial(const PairMeta *__restrict__ meta, const RowChu
     i128 *out = part + (int64_t)ci * d;
     if ((d * esz) % 16 == 0 && ((uintptr_t)base & 15u) == 0) {
         if (dtype == DT_F32) colsum_vec<DT_F32>(base, ch, d, out, ok);
-        else colsum_vec<DT_BF16>(base, ch, d, out, ok);
+        else colsum_bf16(base, ch, d, out, ok);
     } else {
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
             WinAcc wa;
@@ -181,6 +254,75 @@ __device__ __forceinline__ void store_z(void *Z, int64_t idx, double v)
     else reinterpret_cast<unsigned short *>(Z)[idx] = f64_to_bf16_rn(v);
 }
 
+// BF16 storage, one step j of the compensated FP32 dot product u^T x of a row:
+// u_j = uh + ul + e_j with |e_j| <= 2^-48 |u_j|; exact products uh x = p + e;
+// the partial sums of p by TwoSum, their errors, e and ul x summed by a second
+// TwoSum level; fa = sum |p| rounded up.
+__device__ __forceinline__ void dot_step(float x, float uh, float ul, float &fs, float &fc, float &fcc, float &fa)
+{
+    const float p = __fmul_rn(uh, x);
+    const float e = __fmaf_rn(uh, x, -p);
+    const float q = __fmul_rn(ul, x);
+    const float s1 = __fadd_rn(fs, p), bp = __fsub_rn(s1, fs);
+    const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(s1, bp)), __fsub_rn(p, bp));
+    fs = s1;
+    const float wv = __fadd_rn(__fadd_rn(err, e), q);
+    const float c1 = __fadd_rn(fc, wv), bw = __fsub_rn(c1, fc);
+    fcc = __fadd_rn(fcc, __fadd_rn(__fsub_rn(fc, __fsub_rn(c1, bw)), __fsub_rn(wv, bw)));
+    fc = c1;
+    fa = __fadd_ru(fa, fabsf(p));
+}
+
+// a = -2 (ah + al) with ah + al = fs + (fc + fcc) (TwoSum); its distance to
+// -2 c_chain is at most dl = 2 delta:
+//   delta = A (2^-45 (d + 8) + 2 (d 2^-24)^3) + 2^-100, A = sum |uh x| (rounded up)
+// which covers the FP32 roundings of the second level, the first-level error
+// sums, the dropped ul x and e_j terms, |c_chain - u^T x| <= d 2^-53 sum |u x|,
+// and products below the normal range
+__device__ __forceinline__ void dot_finish(float fs, float fc, float fcc, float fa, int d, float &ah2, float &al2,
+                                           float &dl)
+{
+    const float t = __fadd_rn(fc, fcc);
+    const float ah = __fadd_rn(fs, t), bt = __fsub_rn(ah, fs);
+    const float al = __fadd_rn(__fsub_rn(fs, __fsub_rn(ah, bt)), __fsub_rn(t, bt));
+    const float dd = (float)d;
+    const float g3 = __fmul_ru(dd, 0x1p-24f);
+    const float K = __fadd_ru(__fmul_ru(__fadd_ru(dd, 8.0f), 0x1p-45f), __fmul_ru(2.0f, __fmul_ru(g3, __fmul_ru(g3, g3))));
+    ah2 = -2.0f * ah;
+    al2 = -2.0f * al;
+    dl = __fmul_ru(2.0f, __fmaf_ru(fa, K, 0x1p-100f));
+}
+
+// BF16 storage, one reflected element v = fl64(a u_j + x), a = -2 c_chain,
+// from the compensated values: x + (ah + al)(uh + ul) = S + yl = V + t up to
+// 2^-44 (|x| + |P|), plus |u_j| dl for the distance of ah + al to a and
+// 2^-52 |v| for the FP64 rounding (E).  With m the BF16 midpoint in |V|'s
+// interval, |v| - m = (|V| - m) +- t +- E and |V| - m is exact: outside +-E
+// (and with E + |t| under a quarter step) the sign decides the rounding
+// (sure = true); otherwise (or for tiny V) the caller decides with the FP64
+// chain and expression.
+__device__ __forceinline__ unsigned short reflect_bf16_fast(float x, float ah, float al, float dl, float uh, float ul,
+                                                            float auh, bool &sure)
+{
+    const float P = __fmul_rn(ah, uh), Pe = __fmaf_rn(ah, uh, -P);
+    const float cross = __fmaf_rn(ah, ul, __fmul_rn(al, uh));
+    const float S = __fadd_rn(x, P), bp = __fsub_rn(S, x);
+    const float Se = __fadd_rn(__fsub_rn(x, __fsub_rn(S, bp)), __fsub_rn(P, bp));
+    const float yl = __fadd_rn(Se, __fadd_rn(Pe, cross));
+    // S + yl renormalised (TwoSum) to V + t with |t| <= 2^-24 |V|: under cancellation
+    // yl can span several BF16 steps of the result
+    const float V = __fadd_rn(S, yl), bv = __fsub_rn(V, S);
+    const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(V, bv)), __fsub_rn(yl, bv));
+    const float E = __fmaf_ru(__fadd_ru(fabsf(x), fabsf(P)), 0x1p-43f, __fmaf_ru(auh, __fmul_ru(dl, 1.01f), 0x1p-100f));
+    const float aV = fabsf(V);
+    const uint32_t tr = __float_as_uint(aV) & 0xffff0000u;
+    const float dist = __fadd_rn(__fsub_rn(aV, __uint_as_float(tr | 0x8000u)), V < 0.0f ? -t : t);
+    // a quarter of V's BF16 step: |v| stays between the neighbouring midpoints
+    const float q4 = __uint_as_float((__float_as_uint(aV) & 0x7f800000u) - (9u << 23));
+    sure = aV >= 0x1p-100f && fabsf(dist) > __fmul_ru(E, 1.0001f) && __fadd_ru(E, fabsf(t)) < q4;
+    return (unsigned short)(((__float_as_uint(V) & 0x80000000u) | (tr + (dist > 0.0f ? 0x10000u : 0u))) >> 16);
+}
+
 // The exact FP64 dot product c = u^T x_r of the reference, a sequential FMA
 // chain over j = 0..d-1, for the rare elements a BF16-storage reflection cannot
 // decide from its compensated FP32 evaluation; -2c is kept in shared memory.
@@ -255,20 +397,7 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
                 if (DT == DT_F32) {
                     for (int jj = 0; jj < w; ++jj) c = __fma_rn(us[jj], f32_to_f64(xs[r][jj]), c);
                 } else {
-                    for (int jj = 0; jj < w; ++jj) {
-                        const float x = xs[r][jj], uh = uh_s[jj];
-                        const float p = __fmul_rn(uh, x);
-                        const float e = __fmaf_rn(uh, x, -p);
-                        const float q = __fmul_rn(ul_s[jj], x);
-                        const float s1 = __fadd_rn(fs, p), bp = __fsub_rn(s1, fs);
-                        const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(s1, bp)), __fsub_rn(p, bp));
-                        fs = s1;
-                        const float wv = __fadd_rn(__fadd_rn(err, e), q);
-                        const float c1 = __fadd_rn(fc, wv), bw = __fsub_rn(c1, fc);
-                        fcc = __fadd_rn(fcc, __fadd_rn(__fsub_rn(fc, __fsub_rn(c1, bw)), __fsub_rn(wv, bw)));
-                        fc = c1;
-                        fa = __fadd_ru(fa, fabsf(p));
-                    }
+                    for (int jj = 0; jj < w; ++jj) dot_step(xs[r][jj], uh_s[jj], ul_s[jj], fs, fc, fcc, fa);
                 }
             }
             __syncthreads();
@@ -277,21 +406,7 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
         if (DT == DT_F32) {
             cs[r] = -2.0 * c;  // exact scaling by -2
         } else {
-            // a = -2 (ah + al) with ah + al = fs + (fc + fcc) (TwoSum); its distance to
-            // -2 c_chain is at most dl = 2 delta:
-            //   delta = A (2^-45 (d + 8) + 2 (d 2^-24)^3) + 2^-100, A = sum |uh x| (rounded up)
-            // which covers the FP32 roundings of the second level, the first-level error
-            // sums, the dropped ul x and e_j terms, |c_chain - u^T x| <= d 2^-53 sum |u x|,
-            // and products below the normal range
-            const float t = __fadd_rn(fc, fcc);
-            const float ah = __fadd_rn(fs, t), bt = __fsub_rn(ah, fs);
-            const float al = __fadd_rn(__fsub_rn(fs, __fsub_rn(ah, bt)), __fsub_rn(t, bt));
-            const float dd = (float)d;
-            const float g3 = __fmul_ru(dd, 0x1p-24f);
-            const float K = __fadd_ru(__fmul_ru(__fadd_ru(dd, 8.0f), 0x1p-45f), __fmul_ru(2.0f, __fmul_ru(g3, __fmul_ru(g3, g3))));
-            ah_s[r] = -2.0f * ah;
-            al_s[r] = -2.0f * al;
-            dl_s[r] = __fmul_ru(2.0f, __fmaf_ru(fa, K, 0x1p-100f));
+            dot_finish(fs, fc, fcc, fa, d, ah_s[r], al_s[r], dl_s[r]);
             chain_s[r] = 0;
         }
         __syncthreads();
@@ -316,42 +431,15 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
             const uint32_t xb = xv[k];
             float zf;
             if (reflect && DT == DT_BF16) {
-                // v = fl64(a u_j + x), a = -2 c_chain, from the compensated values:
-                // x + (ah + al)(uh + ul) = S + yl = V + t up to 2^-44 (|x| + |P|), plus
-                // |u_j| dl for the distance of ah + al to a and 2^-52 |v| for the FP64
-                // rounding (E).  With m the BF16 midpoint in |V|'s interval, |v| - m =
-                // (|V| - m) +- t +- E and |V| - m is exact: outside +-E (and with E + |t|
-                // under a quarter step) the sign decides the rounding; otherwise (or for
-                // tiny V) the FP64 chain and expression decide.
-                const float x = __uint_as_float(xb);
-                const float ah = ah_s[r];
-                const float P = __fmul_rn(ah, uh), Pe = __fmaf_rn(ah, uh, -P);
-                const float cross = __fmaf_rn(ah, ul, __fmul_rn(al_s[r], uh));
-                const float S = __fadd_rn(x, P), bp = __fsub_rn(S, x);
-                const float Se = __fadd_rn(__fsub_rn(x, __fsub_rn(S, bp)), __fsub_rn(P, bp));
-                const float yl = __fadd_rn(Se, __fadd_rn(Pe, cross));
-                // S + yl renormalised (TwoSum) to V + t with |t| <= 2^-24 |V|: under cancellation
-                // yl can span several BF16 steps of the result
-                const float V = __fadd_rn(S, yl), bv = __fsub_rn(V, S);
-                const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(V, bv)), __fsub_rn(yl, bv));
-                const float E = __fmaf_ru(__fadd_ru(fabsf(x), fabsf(P)), 0x1p-43f,
-                                          __fmaf_ru(auh, __fmul_ru(dl_s[r], 1.01f), 0x1p-100f));
-                const float aV = fabsf(V);
-                const uint32_t tr = __float_as_uint(aV) & 0xffff0000u;
-                const float dist = __fadd_rn(__fsub_rn(aV, __uint_as_float(tr | 0x8000u)), V < 0.0f ? -t : t);
-                // a quarter of V's BF16 step: |v| stays between the neighbouring midpoints
-                const float q4 = __uint_as_float((__float_as_uint(aV) & 0x7f800000u) - (9u << 23));
-                unsigned short zb;
-                if (aV >= 0x1p-100f && fabsf(dist) > __fmul_ru(E, 1.0001f) && __fadd_ru(E, fabsf(t)) < q4) {
-                    zb = (unsigned short)(((__float_as_uint(V) & 0x80000000u) | (tr + (dist > 0.0f ? 0x10000u : 0u))) >>
-                                          16);
-                } else {
+                bool sure;
+                unsigned short zb = reflect_bf16_fast(__uint_as_float(xb), ah_s[r], al_s[r], dl_s[r], uh, ul, auh, sure);
+                if (!sure) {
                     if (!((volatile int *)chain_s)[r]) {  // another column's thread may be here too
                         ((volatile double *)cs)[r] = reflect_chain<DT>(src, ch.row0 + r, d, up);
                         __threadfence_block();
                         ((volatile int *)chain_s)[r] = 1;
                     }
-                    zb = f64_to_bf16_rn(__fma_rn(((volatile double *)cs)[r], uj, f32_to_f64(x)));
+                    zb = f64_to_bf16_rn(__fma_rn(((volatile double *)cs)[r], uj, f32_to_f64(__uint_as_float(xb))));
                 }
                 reinterpret_cast<unsigned short *>(Z)[zi] = zb;
                 zf = __uint_as_float((uint32_t)zb << 16);
@@ -372,6 +460,166 @@ __global__ void __launch_bounds__(128, 8) k_reflect(const PairMeta *__restrict__
         // an upper bound of the column's L1 norm in units of 2^-40 (integer atomics:
         // exact and order-free, so the slice grids do not depend on the schedule)
         if (colL1) atomicAdd(colL1 + (int64_t)ch.pair * o.d_pad + j, __float2ull_ru(__fmul_rn(l1, 0x1p40f)));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same reflection for BF16 storage with d a multiple of 8, d <= 1024 and
+// 16-byte aligned rows: the same arithmetic per row and per element, with
+// 16-byte loads and stores and the next loads in flight while the current
+// ones are consumed.  Dot products: tiles of 128 rows x 32 columns staged in
+// shared memory (two buffers; the next tile is loaded into registers during
+// the current tile's steps), one row per thread in column order.  Element
+// pass: thread g owns the 8-column group g for every row of the chunk (its
+// u values, maxima and L1 sums stay in registers), four rows per batch with
+// the next batch in flight.
+// ---------------------------------------------------------------------------
+// The rare element the compensated evaluation cannot decide: the row's FP64
+// chain (computed once per row by whichever thread needs it first) and the
+// FP64 expression.  Out of line, so the unrolled element loop stays small.
+__device__ __noinline__ uint32_t reflect_v_fallback(const void *src, int row, int r, int d, const double *up, int j,
+                                                    uint32_t xb, double *cs, int *chain_s)
+{
+    if (!((volatile int *)chain_s)[r]) {  // another column's thread may be here too
+        ((volatile double *)cs)[r] = reflect_chain<DT_BF16>(src, row, d, up);
+        __threadfence_block();
+        ((volatile int *)chain_s)[r] = 1;
+    }
+    return f64_to_bf16_rn(__fma_rn(((volatile double *)cs)[r], up[j], f32_to_f64(__uint_as_float(xb))));
+}
+
+constexpr int RV_T = 32;               // columns per dot-product tile
+constexpr int RV_Q = RV_T / 8;         // 16-byte pieces per tile row
+constexpr int RV_RB = 4;               // rows per element-pass batch
+
+__global__ void __launch_bounds__(128, 4) k_reflect_v(const PairMeta *__restrict__ meta,
+                                                     const RowChunk *__restrict__ chunks, int c0, const RunOpts o,
+                                                     const PairState *__restrict__ st, const double *__restrict__ u,
+                                                     void *__restrict__ Z, unsigned int *__restrict__ colmax,
+                                                     unsigned long long *__restrict__ colL1)
+{
+    __shared__ uint4 xt[2][CHUNK_ROWS][RV_Q + 1];  // +1: conflict-free row reads
+    __shared__ float uh_s[1024], ul_s[1024];
+    __shared__ double cs[CHUNK_ROWS];
+    __shared__ float ah_s[CHUNK_ROWS], al_s[CHUNK_ROWS], dl_s[CHUNK_ROWS];
+    __shared__ int chain_s[CHUNK_ROWS];
+    const RowChunk ch = chunks[c0 + (int)blockIdx.x];
+    const PairMeta pm = meta[ch.pair];
+    if (st[ch.pair].status != ST_OK) return;
+    const int d = o.d, G = d / 8, t = threadIdx.x;
+    const uint4 *src = reinterpret_cast<const uint4 *>(ch.side ? pm.Y : pm.X) + (int64_t)ch.row0 * G;
+    uint4 *dst = reinterpret_cast<uint4 *>(Z) + (pm.z_row + (ch.side ? pm.n : 0) + ch.row0) * (int64_t)G;
+    const bool reflect = !st[ch.pair].skipped && (ch.side == o.reflect_side);
+    const double *up = u + (int64_t)ch.pair * d;
+    const int nr = ch.nrows;
+
+    if (reflect) {
+        for (int j = t; j < d; j += blockDim.x) {
+            const double uu = up[j];
+            const float h = __double2float_rn(uu);
+            uh_s[j] = h;
+            ul_s[j] = __double2float_rn(__dsub_rn(uu, (double)h));
+        }
+        // piece k = t + 128 i of a tile: row k / RV_Q, 8-column piece k % RV_Q
+        const int ntile = (d + RV_T - 1) / RV_T;
+        uint4 pre[RV_Q];
+        auto load_tile = [&](int tt) {
+#pragma unroll
+            for (int i = 0; i < RV_Q; ++i) {
+                const int k = t + 128 * i, r = k / RV_Q, q = k % RV_Q, g = tt * RV_Q + q;
+                pre[i] = (r < nr && g < G) ? __ldg(src + (int64_t)r * G + g) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        load_tile(0);
+        float fs = 0.0f, fc = 0.0f, fcc = 0.0f, fa = 0.0f;
+        for (int tt = 0; tt < ntile; ++tt) {
+            uint4 (*buf)[RV_Q + 1] = xt[tt & 1];
+#pragma unroll
+            for (int i = 0; i < RV_Q; ++i) {
+                const int k = t + 128 * i;
+                buf[k / RV_Q][k % RV_Q] = pre[i];
+            }
+            __syncthreads();  // the tile is in; uh_s/ul_s too (first tile)
+            if (tt + 1 < ntile) load_tile(tt + 1);
+            if (t < nr) {
+                const int j0 = tt * RV_T, w = min(RV_T, d - j0);
+                for (int q = 0; q < w / 8; ++q) {
+                    const uint4 v = buf[t][q];
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x = __uint_as_float((e & 1) ? (wv[e >> 1] & 0xffff0000u) : (wv[e >> 1] << 16));
+                        const int j = j0 + 8 * q + e;
+                        dot_step(x, uh_s[j], ul_s[j], fs, fc, fcc, fa);
+                    }
+                }
+            }
+        }
+        if (t < nr) {
+            dot_finish(fs, fc, fcc, fa, d, ah_s[t], al_s[t], dl_s[t]);
+            chain_s[t] = 0;
+        }
+        __syncthreads();
+    }
+
+    // element pass: thread g < G owns columns 8g .. 8g + 7
+    if (t < G) {
+        float uh[8], ul[8], mx[8], l1[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            uh[e] = reflect ? uh_s[8 * t + e] : 0.0f;
+            ul[e] = reflect ? ul_s[8 * t + e] : 0.0f;
+            mx[e] = l1[e] = 0.0f;
+        }
+        uint4 cur[RV_RB], nxt[RV_RB];
+#pragma unroll
+        for (int k = 0; k < RV_RB; ++k) cur[k] = k < nr ? __ldg(src + (int64_t)k * G + t) : make_uint4(0u, 0u, 0u, 0u);
+        for (int rb = 0; rb < nr; rb += RV_RB) {
+#pragma unroll
+            for (int k = 0; k < RV_RB; ++k) {
+                const int r = rb + RV_RB + k;
+                nxt[k] = r < nr ? __ldg(src + (int64_t)r * G + t) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < RV_RB; ++k) {
+                const int r = rb + k;
+                if (r >= nr) break;
+                const uint32_t wv[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+                uint32_t ow[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    uint32_t zz[2];
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const int e = 2 * h + s2;
+                        const uint32_t xb = s2 ? (wv[h] & 0xffff0000u) : (wv[h] << 16);
+                        uint32_t zb = xb >> 16;
+                        if (reflect) {
+                            bool sure;
+                            zb = reflect_bf16_fast(__uint_as_float(xb), ah_s[r], al_s[r], dl_s[r], uh[e], ul[e],
+                                                   fabsf(uh[e]), sure);
+                            if (!sure)
+                                zb = reflect_v_fallback(ch.side ? pm.Y : pm.X, ch.row0 + r, r, d, up, 8 * t + e, xb, cs,
+                                                        chain_s);
+                        }
+                        const float zf = __uint_as_float(zb << 16);
+                        mx[e] = fmaxf(mx[e], fabsf(zf));
+                        l1[e] = __fadd_ru(l1[e], fabsf(zf));
+                        zz[s2] = zb;
+                    }
+                    ow[h] = zz[0] | (zz[1] << 16);
+                }
+                dst[(int64_t)r * G + t] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+            }
+#pragma unroll
+            for (int k = 0; k < RV_RB; ++k) cur[k] = nxt[k];
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t ci = (int64_t)ch.pair * o.d_pad + 8 * t + e;
+            if (colmax) atomicMax(colmax + ci, __float_as_uint(mx[e]));
+            if (colL1) atomicAdd(colL1 + ci, __float2ull_ru(__fmul_rn(l1[e], 0x1p40f)));
+        }
     }
 }
 
@@ -600,7 +848,7 @@ __device__ __noinline__ i128 zs_slow_column(uint32_t w0, uint32_t w1, uint32_t w
     return warp_sum_i128(sl);
 }
 
-__global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restrict__ meta,
+__global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restrict__ meta,
                                                     const RowChunk *__restrict__ chunks, int c0, const RunOpts o,
                                                     const PairState *__restrict__ st, const uint4 *__restrict__ Z,
                                                     const unsigned long long *__restrict__ colL1,
@@ -653,7 +901,10 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
                                         : e == 4 ? l45.x : e == 5 ? l45.y : e == 6 ? l67.x : l67.y;
             const L1Grid G = l1_grid(lb, pm.N);
             float kf[4], k2f[4];
-            int sk = 0, sk2 = 0;
+            // the slice multiples k, k2 are integers whose magnitudes over all of the
+            // pair's tokens sum to less than 2^24 (l1_grid), so FP32 sums of any of them
+            // are exact; one conversion per lane instead of one per value
+            float fk = 0.0f, fk2 = 0.0f;
             float ra1 = 0.0f, ra2 = 0.0f;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -661,13 +912,14 @@ __global__ void __launch_bounds__(256, 4) k_zstats_tok(const PairMeta *__restric
                 const float z = __uint_as_float((e & 1) ? (wd & 0xffff0000u) : (wd << 16));  // 0 where !ok
                 float r1, r2;
                 l1_split(z, G, kf[i], k2f[i], r1, r2);
-                sk += __float2int_rz(kf[i]);  // |k| <= 2^24: exact
-                sk2 += __float2int_rz(k2f[i]);
+                fk += kf[i];
+                fk2 += k2f[i];
                 ra1 = __fadd_ru(ra1, fabsf(r1));
                 ra2 = __fadd_ru(ra2, fabsf(r2));  // 0 iff every second residual is 0
                 kf[i] = __fmul_rn(kf[i], G.g);    // the slice values (exact)
                 k2f[i] = __fmul_rn(k2f[i], G.g2);
             }
+            const int sk = __float2int_rz(fk), sk2 = __float2int_rz(fk2);
             // the slice values have at most 8 significant bits: the high halves of
             // their FP32 bits are their BF16 bits
             const uint32_t hp0 = __byte_perm(__float_as_uint(kf[0]), __float_as_uint(kf[1]), 0x7632);
@@ -862,11 +1114,13 @@ void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, con
 
 void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                     const PairState *pst, const double *u, void *Z, unsigned int *colmax,
-                    unsigned long long *colL1, cudaStream_t st)
+                    unsigned long long *colL1, bool vec16, cudaStream_t st)
 {
     if (sp.c1 <= sp.c0) return;
     const unsigned nc = (unsigned)(sp.c1 - sp.c0);
     if (o.dtype == DT_F32) k_reflect<DT_F32><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax, colL1);
+    else if (vec16 && o.d % 8 == 0 && o.d <= 1024)
+        k_reflect_v<<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax, colL1);
     else k_reflect<DT_BF16><<<nc, 128, 0, st>>>(meta, chunks, sp.c0, o, pst, u, Z, colmax, colL1);
 }
 
@@ -899,6 +1153,9 @@ void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, con
 
 void set_align_attributes()
 {
+    // the reflection's shared-memory tiles: keep the largest carveout so that the
+    // register limit, not shared memory, decides how many blocks an SM holds
+    cudaFuncSetAttribute(k_reflect_v, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     const int big = 200 * 1024;
     cudaFuncSetAttribute(k_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_tobs, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

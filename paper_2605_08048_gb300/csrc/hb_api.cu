@@ -94,7 +94,7 @@ struct hb_ctx {
     size_t tbuf_cap = 0;
     // options (hb_ctx_set_option)
     uint64_t wait_ns = 4000000000ull;  // limit of every device barrier wait
-    int32_t s1_max = 8192;             // BF16: pairs with n + m <= s1_max start with the single-slice pass
+    int32_t s1_max = 65536;            // BF16: pairs with n + m <= s1_max start with the single-slice pass
     int32_t withhold = 0;              // test hook: the next tensor-core call withholds one barrier arrival
 };
 
@@ -243,7 +243,7 @@ static inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // Context options a plan is built with (defaults without a context).
 struct CtxOpts {
     uint64_t wait_ns = 4000000000ull;
-    int32_t s1_max = 8192;
+    int32_t s1_max = 65536;
     int32_t withhold = 0;
 };
 
@@ -278,6 +278,16 @@ struct Plan {
     int lc_pair[LABEL_CHUNKS + 1] = {};
     int lc_item[LABEL_CHUNKS + 1] = {};
 };
+
+// every pair's X and Y rows and the rows of Z start on 16-byte boundaries
+static bool rows_16b_aligned(const Plan &pl, const void *Z)
+{
+    const size_t row = (size_t)pl.o.d * (pl.o.dtype == HB_F32 ? 4 : 2);
+    if (row % 16 != 0 || ((uintptr_t)Z & 15u) != 0) return false;
+    for (const PairMeta &pm : pl.meta)
+        if ((((uintptr_t)pm.X | (uintptr_t)pm.Y) & 15u) != 0) return false;
+    return true;
+}
 
 static hb_status validate_common(int64_t d, int32_t dtype)
 {
@@ -707,7 +717,8 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         // steps 1-3 (column maxima feed the slice scales and the exact-sum windows)
         launch_colsum(b.meta, b.chunks, sp, d, o.dtype, b.part, b.s, b.bad, s);
         launch_axis(b.meta, sp, o, b.s, b.bad, b.st, b.u, s);
-        launch_reflect(b.meta, b.chunks, sp, o, b.st, b.u, Z, b.colmax, features ? nullptr : b.colL1, s);
+        launch_reflect(b.meta, b.chunks, sp, o, b.st, b.u, Z, b.colmax, features ? nullptr : b.colL1,
+                       rows_16b_aligned(pl, Z), s);
         CK(cudaGetLastError());
         // step 4: Z statistics, fixed-point slices, T_obs
         if (pieces == 1) xmark(ex, 1);
@@ -876,7 +887,7 @@ static hb_status run_on(hb_ctx *c, Plan &pl, const void *xy_host, size_t xy_byte
             mark(c, 0, s);
             launch_colsum(b.meta, b.chunks, all, d, o.dtype, b.part, b.s, b.bad, s);
             launch_axis(b.meta, all, o, b.s, b.bad, b.st, b.u, s);
-            launch_reflect(b.meta, b.chunks, all, o, b.st, b.u, Z, nullptr, nullptr, s);
+            launch_reflect(b.meta, b.chunks, all, o, b.st, b.u, Z, nullptr, nullptr, rows_16b_aligned(pl, Z), s);
             CK(cudaGetLastError());
             if (u_out) CK(cudaMemcpyAsync(u_out, b.u, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
             if (skipped_out) {

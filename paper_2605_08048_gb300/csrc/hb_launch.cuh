@@ -21,9 +21,11 @@ void launch_colsum(const PairMeta *meta, const RowChunk *chunks, const PairSpan 
                    i128 *s, int *bad, cudaStream_t st);
 void launch_axis(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *s, const int *bad,
                  PairState *pst, double *u, cudaStream_t st);
+// vec16: every pair's X, Y and Z rows start on 16-byte boundaries (BF16 with
+// d % 8 == 0 and d <= 1024 then takes the 16-byte kernel)
 void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                     const PairState *pst, const double *u, void *Z, unsigned int *colmax,
-                    unsigned long long *colL1, cudaStream_t st);
+                    unsigned long long *colL1, bool vec16, cudaStream_t st);
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax,
                    const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,

@@ -165,7 +165,9 @@ extern "C" hb_status hb_align_noalloc(const void *X, int64_t n, const void *Y, i
     const PairSpan all{0, 1, 0, nch};
     launch_colsum(meta, chunks, all, (int)d, dtype, part, sums, bad, s);
     launch_axis(meta, all, o, sums, bad, st, u, s);
-    launch_reflect(meta, chunks, all, o, st, u, Z_out, nullptr, nullptr, s);
+    const bool vec16 = (d * (dtype == HB_F32 ? 4 : 2)) % 16 == 0 &&
+                       (((uintptr_t)X | (uintptr_t)Y | (uintptr_t)Z_out) & 15u) == 0;
+    launch_reflect(meta, chunks, all, o, st, u, Z_out, nullptr, nullptr, vec16, s);
     if (cudaGetLastError() != cudaSuccess) return err(HB_ERR_CUDA, "hb_align_noalloc: a kernel launch failed");
     if (u_out && cudaMemcpyAsync(u_out, u, sizeof(double) * (size_t)d, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
         cudaGetLastError();

@@ -118,12 +118,10 @@ def triage(ctx: H.Context, net: H.MLP, batch, opts: H.hb_opts, alpha: float = 0.
     t_sub = 0.0
     p_full = np.full(P, np.nan)
     if len(sub):
-        X2, n2, m2 = pack(XY, batch.n, batch.m, sub)
-        torch.cuda.synchronize()
+        # gathering the routed pairs into their own packed batch is part of the triage's cost
         t0 = time.perf_counter()
-        r = H.hb_perm_test_batched(ctx, X2, n2, m2, opts)
+        p_full[sub] = test_subset(ctx, XY, batch.n, batch.m, sub, opts)
         t_sub = time.perf_counter() - t0
-        p_full[sub] = [x["p"] for x in r]
     t_all = float("nan")
     if evaluate_all:
         torch.cuda.synchronize()
@@ -139,6 +137,14 @@ def triage(ctx: H.Context, net: H.MLP, batch, opts: H.hb_opts, alpha: float = 0.
         else float("nan")
     return TriageReport(P, int(full.sum()), int(audit_mask.sum()), int((~full).sum()), audit_err, err_skipped,
                         t_feat, t_sub, t_all, p_hat, p_all if evaluate_all else p_full)
+
+
+def test_subset(ctx: H.Context, XY: torch.Tensor, n, m, idx, opts: H.hb_opts) -> np.ndarray:
+    """The full test (hb_perm_test_batched) of the pairs `idx` of a packed
+    device batch, gathered into a packed batch of their own; their p-values."""
+    X2, n2, m2 = pack(XY, n, m, idx)
+    r = H.hb_perm_test_batched(ctx, X2, n2, m2, opts)
+    return np.array([x["p"] for x in r])
 
 
 def pack(XY: torch.Tensor, n, m, idx):

@@ -9,10 +9,12 @@ GPU's own statistics leave open:
   decided exactly by the oracle, and the GPU count must equal the count those
   exact decisions and the clear-cut rest give;
 - batched (4096 pairs, lognormal sizes, d = 768 BF16, B = 9999): the whole
-  batch on the GPU, a random sample of pairs through the oracle, counts and
-  p bit for bit;
+  batch on the GPU, every pair's count and p bit for bit against the oracle's
+  results stored by tests/golden/make_batched4096_oracle.py;
 - Type-I sweep (n = m = 500, d = 768 BF16, B = 4999, mean directions 0-90
   degrees): a 100-pair subset, aligned and naive, counts bit for bit."""
+import os
+
 import numpy as np
 import pytest
 
@@ -48,6 +50,10 @@ def test_large_pair_sampled_parity(ctx, case):
     n, m = X.shape[0], Y.shape[0]
     B = 100000
     Xd, Yd = dev(X), dev(Y)
+    # both slices at once: every reported T_b is then within the two-slice band
+    # (the single-slice pass and the gathered pass are checked against the
+    # oracle's T_b of every relabelling in test_gpu_passes.py)
+    H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, 0)
     # aligned Z, bit for bit
     Z, _, _ = H.hb_align(ctx, Xd, Yd)
     st, Zref, _, _, _ = O.align(X, Y)
@@ -78,23 +84,40 @@ def test_large_pair_sampled_parity(ctx, case):
     exact_near = int(dec[np.searchsorted(b_list, near)].sum())
     assert res["count"] == exceed_clear + exact_near
     assert res["p"] == (1 + res["count"]) / (B + 1)
+    H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, 65536)
     print(f"\nlarge pair ({case}): count {res['count']} of {B}, {len(near)} relabellings decided by the oracle, "
           f"{res['n_rechecked']} rechecked on the GPU")
     if case == "null":
         assert 0 < res["count"] < B and len(near) > 0
 
 
-def test_batched_full_size_sampled_parity(ctx):
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batched4096_b9999_oracle.txt")
+
+
+def _golden_batched():
+    rows = [line.split() for line in open(GOLDEN) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 4096, "the stored oracle results must cover every pair (make_batched4096_oracle.py)"
+    return rows
+
+
+@pytest.mark.parametrize("path", [H.HB_PATH_MIXED_2SM, H.HB_PATH_MIXED])
+def test_batched_full_size_every_pair(ctx, path):
+    """The benchmark's whole workload (4096 pairs, B = 9999, the launch
+    configuration the benchmark times) against the oracle's stored results for
+    every pair: sizes, status, count and p bit for bit, plus T_obs of a sample
+    recomputed by the oracle."""
+    rows = _golden_batched()
     b = synth.workload_batched(seed=1237, P=4096)
-    XY = dev(b.XY)
-    res = H.hb_perm_test_batched(ctx, XY, b.n, b.m, H.make_opts(B=9999, seed=1))
-    assert all(r["status"] == 0 for r in res)
+    res = H.hb_perm_test_batched(ctx, dev(b.XY), b.n, b.m, H.make_opts(B=9999, seed=1, path=path))
+    for k, (pi, n, m, st, cnt, p) in enumerate(rows):
+        assert int(pi) == k and int(n) == b.n[k] and int(m) == b.m[k]
+        assert res[k]["status"] == int(st)
+        assert res[k]["count"] == int(cnt), (k, res[k]["count"], cnt)
+        assert res[k]["p"] == float(p)
     rng = np.random.default_rng(8)
-    pick = np.sort(rng.choice(4096, 12, replace=False))
-    for p in pick:
+    for p in np.sort(rng.choice(4096, 4, replace=False)):
         X, Y = b.pair(int(p))
         ref, _, _ = O.perm_test(X, Y, O.opts(B=9999, seed=1))
-        assert res[p]["count"] == ref["count"] and res[p]["p"] == ref["p"]
         assert res[p]["T_obs"] == pytest.approx(ref["T_obs"], rel=1e-12, abs=1e-15)
 
 

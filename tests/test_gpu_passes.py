@@ -39,7 +39,7 @@ def ctx():
     c.close()
 
 
-def _set(ctx, s1_max=8192, wait_ns=4_000_000_000):
+def _set(ctx, s1_max=65536, wait_ns=4_000_000_000):
     H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, s1_max)
     H.set_option(ctx, H.HB_OPT_WAIT_LIMIT_NS, wait_ns)
 

@@ -142,3 +142,20 @@ def test_evaluate_at_scale_small(ctx):
     assert 0.0 <= rep["decision_error_skipped"] <= 0.5 and 0.0 <= rep["audit_decision_error"] <= 1.0
     assert rep["loss_last"] < rep["loss_first"]
     assert rep["seconds_full_all"] > 0 and rep["speedup"] > 0
+
+
+def test_in_band_pairs_match_oracle(ctx):
+    """The pairs the triage routes to the full test are gathered into a packed
+    batch of their own and tested there (TR.test_subset, which TR.triage
+    calls on its in-band and audit pairs): their p-values must equal the
+    oracle's bit for bit, for a ragged subset of a ragged batch."""
+    n = np.array([60, 45, 130, 20, 77, 300, 64, 12, 90, 51, 33, 140], dtype=np.int64)
+    m = np.array([70, 90, 40, 25, 66, 120, 64, 30, 11, 52, 200, 9], dtype=np.int64)
+    b = synth.batch(321, len(n), 128, "bf16", sizes=(n, m))
+    opts = H.make_opts(B=999, seed=5)
+    idx = np.array([1, 2, 5, 6, 9, 11])
+    p = TR.test_subset(ctx, _dev(b.XY), b.n, b.m, idx, opts)
+    for k, pk in zip(idx, p):
+        X, Y = b.pair(int(k))
+        ref, _, _ = O.perm_test(X, Y, O.opts(B=999, seed=5))
+        assert pk == ref["p"]

@@ -9,7 +9,7 @@ import pytest
 
 from paper_2605_08048_gb300 import hbperm as H
 
-CHUNK_ROWS, PIECES, S1_MAX = 128, 8, 8192
+CHUNK_ROWS, PIECES, S1_MAX = 128, 8, 65536
 # relabellings per work item: one 128-row tile for single CTAs, two for CTA pairs
 CLUSTER_TILES = {H.HB_PATH_MIXED: 128, H.HB_PATH_MIXED_NARROW: 128, H.HB_PATH_MIXED_2SM: 2 * 128}
 

@@ -124,3 +124,51 @@ def test_bf16_round_agrees_with_the_c_oracle_rounding():
     want = np.array([O.round_to_bf16(float(x)) for x in v32])
     assert np.array_equal(got, want)
     assert got[-3] == 1.0 and got[-2] == 1.0 + 2.0 ** -6 and got[-1] == 1.0 + 2.0 ** -7  # ties to even, above the tie
+
+
+def test_mlp_forward_hand_computed_network():
+    """A network whose output is known in closed form pins the flat parameter
+    layout (written here from its documented definition, not through
+    `unpack`: [W1 19x256 | b1 256 | W2 256x256 | b2 256 | W3 256x9 | b3 9],
+    weights input-major and row-major), both ReLUs (negative pre-activations
+    must be zeroed) and the BF16 rounding of the weights:
+      hidden1: h_i = relu(F_i - 1) for i < 9, h_19 = 2.5, h_23 = relu(3 F_2), h_30 = relu(-4) = 0;
+      hidden2: g_i = 2 h_i for i < 9, g_19 = 2 h_19, g_23 = h_23, g_30 = relu(h_30 - 3) = 0,
+               g_31 = relu(-1) = 0;
+      output:  y_k = BF16(1 + 2^-10) g_k + 0.5 g_19 + 7 g_30 + 7 g_31 + k with BF16(1 + 2^-10) = 1,
+               plus g_23 for k = 8."""
+    H1, NF, NO = 256, 19, 9
+    oW1, ob1 = 0, NF * H1
+    oW2, ob2 = ob1 + H1, ob1 + H1 + H1 * H1
+    oW3, ob3 = ob2 + H1, ob2 + H1 + H1 * NO
+    total = ob3 + NO
+    assert total == TO.param_layout()[2] == 73225
+    w = np.zeros(total)
+    W1 = lambda i, j: oW1 + i * H1 + j  # noqa: E731
+    W2 = lambda i, j: oW2 + i * H1 + j  # noqa: E731
+    W3 = lambda i, k: oW3 + i * NO + k  # noqa: E731
+    for i in range(9):
+        w[W1(i, i)] = 1.0
+        w[ob1 + i] = -1.0
+        w[W2(i, i)] = 2.0
+        w[W3(i, i)] = 1.0 + 2.0 ** -10  # rounds to 1.0 in BF16
+        w[ob3 + i] = float(i)
+    w[ob1 + 19] = 2.5
+    w[W2(19, 19)] = 2.0
+    for k in range(NO):
+        w[W3(19, k)] = 0.5
+        w[W3(30, k)] = 7.0
+        w[W3(31, k)] = 7.0
+    w[W1(2, 23)] = 3.0   # input 2 -> hidden 23 (a transposed layout would route it elsewhere)
+    w[W2(23, 23)] = 1.0
+    w[W3(23, 8)] = 1.0
+    w[ob1 + 30] = -4.0
+    w[W2(30, 30)] = 1.0
+    w[ob2 + 30] = -3.0
+    w[ob2 + 31] = -1.0
+    rng = np.random.default_rng(4)
+    F = rng.uniform(-2.0, 3.0, size=(6, NF))
+    y, _ = TO.mlp_forward(w, F)
+    want = 2.0 * np.maximum(F[:, :9] - 1.0, 0.0) + 0.5 * 2.0 * 2.5 + np.arange(9.0)
+    want[:, 8] += np.maximum(3.0 * F[:, 2], 0.0)
+    assert np.allclose(y, want, rtol=0, atol=1e-12)
