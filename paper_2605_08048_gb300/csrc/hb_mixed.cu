@@ -60,9 +60,9 @@
 namespace hb {
 
 constexpr int MX_M = 128;            // relabellings per tile (TMEM lanes)
-constexpr int MX_K = 64;             // tokens per stage (one 128-byte swizzle atom of BF16)
+constexpr int MX_K = 64;             // tokens of one 128-byte swizzle atom of BF16 (a stage holds 1 or 2)
 constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
-constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB
+constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB: the A tile of one atom
 constexpr int MX_NACC = 256;         // accumulator columns of one TMEM buffer
 constexpr int MX_BOXR_MIN = 32;      // slice rows per TMA box: at least this, at most 128
 constexpr int MX_APROD = 8;          // A-producer warps (two per row block, one label word each)
@@ -386,7 +386,7 @@ struct ItemInfo {
     bool skip;
 };
 
-template <int DT>
+template <int DT, int KS>
 __device__ __forceinline__ ItemInfo item_info(const MixedParams &P, const WorkItem &w, int CL, int sub)
 {
     ItemInfo I;
@@ -397,7 +397,9 @@ __device__ __forceinline__ ItemInfo item_info(const MixedParams &P, const WorkIt
     I.S = w.mode == MODE_SINGLE ? 1 : (DT == DT_BF16 ? 2 : 3);
     I.cw = P.o.nacc / I.S;
     I.C = (P.o.d + I.cw - 1) / I.cw;
-    I.KC = pm.N_pad / MX_K;
+    // stages of KS tokens; with two atoms per stage the second atom of the last
+    // stage may lie past the pair's tokens: its labels are 0, so it adds nothing
+    I.KC = (pm.N_pad + KS - 1) / KS;
     I.row0 = ((int64_t)w.tile * CL + sub) * MX_M;
     I.nrow = w.mode == MODE_GATHER ? (int64_t)st.n_gather : pm.B;
     // uniform over the cluster: the item's first row decides
@@ -412,16 +414,20 @@ template <int CG, int DT>
 __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
     constexpr int CL = CG;  // CTAs per work item (a cluster of two for CTA pairs)
-    // stages: A (16 KB) + this CTA's B rows (up to 256 x 128 B; CTA pairs hold
-    // half, so the same shared memory holds six stages instead of four)
-    constexpr int STAGE = CG == 2 ? 32 * 1024 : 48 * 1024;
-    constexpr int NS = CG == 2 ? 6 : 4;
+    // stages: AT swizzle atoms of 64 tokens, each an A tile (16 KB) and this CTA's
+    // B rows (up to 256 x 128 B for single CTAs, 128 x 128 B for CTA pairs).  CTA
+    // pairs take two atoms per stage (eight MMAs per barrier handshake, which halves
+    // the handshakes' cost) in three stages of 64 KB; single CTAs one atom in four
+    // stages of 48 KB
+    constexpr int AT = CG == 2 ? 2 : 1;
+    constexpr int KS = AT * MX_K;                  // tokens per stage
+    constexpr int A_BYTES = AT * MX_A_BYTES;
+    constexpr int STAGE = CG == 2 ? 64 * 1024 : 48 * 1024;
+    constexpr int NS = CG == 2 ? 3 : 4;
     static_assert(NS * STAGE <= MX_STAGE_AREA, "stage layout");
     // CG = 2: the odd CTA reports its A stages to the even one in groups of RG
-    // (a cluster-scope release costs about as much as a stage's MMAs, so one per
-    // group rather than per stage); the even CTA waits at the first stage of each
-    // group
-    constexpr int RG = CG == 2 ? 3 : 1;
+    // stages; the even CTA waits at the first stage of each group
+    constexpr int RG = 1;
     static_assert(NS % RG == 0 && NS >= 2 * RG, "relay groups");
 
     extern __shared__ uint8_t smem_raw[];
@@ -488,7 +494,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             const int r_begin = CG == 2 ? (int)(crank & 1u) * (nacc / 2) : 0, r_cnt = nacc / CG;
             const int br = P.box_rows, nb = r_cnt / br;
             for (int it = cid; it < n_work && ok; it += ncl) {
-                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
                 if (I.skip) continue;
                 const PairMeta &pm = P.meta[I.p];
                 // slice row of each box in column tile 0 (tile c adds c * cw)
@@ -504,24 +510,26 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                             ok = false;
                             break;
                         }
-                        const int x = (int)(pm.z_row + kc * MX_K);
-                        const uint32_t bdst = sbase + stage * STAGE + MX_A_BYTES;
+                        const int x0 = (int)(pm.z_row + kc * KS);
+                        const uint32_t bdst = sbase + stage * STAGE + A_BYTES;
                         if (CG == 1) {
-                            mbar_arrive_expect_tx(full(stage), (uint32_t)r_cnt * 128u);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                if (k >= nb) break;
-                                tma_load_2d(bdst + (uint32_t)(k * br) * 128u, &tmap, x, yb[k] + c * I.cw, full(stage));
-                            }
-                        } else {
+                            mbar_arrive_expect_tx(full(stage), (uint32_t)(AT * r_cnt) * 128u);
+                        } else if (leader) {
                             // each CTA of the pair loads its half into its own shared memory and
                             // the even CTA's barrier counts both halves
-                            if (leader) mbar_arrive_expect_tx(full(stage), (uint32_t)nacc * 128u);
-                            const uint32_t bar = mapa_rank(full(stage), crank & ~1u);
+                            mbar_arrive_expect_tx(full(stage), (uint32_t)(AT * nacc) * 128u);
+                        }
+                        const uint32_t bar = CG == 1 ? full(stage) : mapa_rank(full(stage), crank & ~1u);
+#pragma unroll
+                        for (int a = 0; a < AT; ++a) {
+                            const uint32_t adst = bdst + (uint32_t)(a * r_cnt) * 128u;  // atom a's rows
 #pragma unroll
                             for (int k = 0; k < 8; ++k) {
                                 if (k >= nb) break;
-                                tma_load_2d_pair(bdst + (uint32_t)(k * br) * 128u, &tmap, x, yb[k] + c * I.cw, bar);
+                                if (CG == 1) tma_load_2d(adst + (uint32_t)(k * br) * 128u, &tmap, x0 + a * MX_K,
+                                                         yb[k] + c * I.cw, bar);
+                                else tma_load_2d_pair(adst + (uint32_t)(k * br) * 128u, &tmap, x0 + a * MX_K,
+                                                      yb[k] + c * I.cw, bar);
                             }
                         }
                         ++issued;
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             bool ok = true;
             int pending = -1;  // first stage of a group not reported yet
             for (int it = cid; it < n_work && ok; it += ncl) {
-                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
                 if (I.skip) continue;
                 for (int c = 0; c < I.C && ok; ++c) {
                     for (int kc = 0; kc < I.KC; ++kc) {
@@ -589,12 +597,13 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             // bytes, so each MMA's descriptors are two integer adds away
             const uint32_t dhi = (uint32_t)(sw128_desc(sbase) >> 32);
             const uint32_t alo0 = (uint32_t)sw128_desc(sbase);
-            constexpr uint32_t STEP = STAGE >> 4, BOFF = MX_A_BYTES >> 4;
+            constexpr uint32_t STEP = STAGE >> 4, BOFF = A_BYTES >> 4, AOFF = MX_A_BYTES >> 4;
+            const uint32_t BAOFF = (uint32_t)(nacc / CG) * 8u;  // one atom of this CTA's B rows, 16-byte units
             int stage = 0, abuf = 0;
             uint32_t phase = 0, aphase = 0, alo = alo0;
             bool ok = true;
             for (int it = cid; it < n_work && ok; it += ncl) {
-                const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+                const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
                 if (I.skip) continue;
                 for (int c = 0; c < I.C && ok; ++c) {
                     if (!mbar_wait(acc_empty(abuf), aphase ^ 1u, P.timeout, lim)) {
@@ -611,9 +620,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         }
                         tc_fence_after();
 #pragma unroll
-                        for (int k = 0; k < MX_K / 16; ++k) {
-                            const uint64_t ad = ((uint64_t)dhi << 32) | (alo + 2u * k);
-                            const uint64_t bd = ((uint64_t)dhi << 32) | (alo + BOFF + 2u * k);
+                        for (int k = 0; k < KS / 16; ++k) {
+                            const uint32_t a = (uint32_t)(k >> 2), kk = (uint32_t)(k & 3);
+                            const uint64_t ad = ((uint64_t)dhi << 32) | (alo + a * AOFF + 2u * kk);
+                            const uint64_t bd = ((uint64_t)dhi << 32) | (alo + BOFF + a * BAOFF + 2u * kk);
                             if (CG == 2) umma_bf16_pair(dt, ad, bd, idesc, (kc | k) != 0 ? 1u : 0u);
                             else umma_bf16(dt, ad, bd, idesc, (kc | k) != 0 ? 1u : 0u);
                         }
@@ -649,7 +659,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         bool ok = true;
         bool withheld = false;
         for (int it = cid; it < n_work && ok; it += ncl) {
-            const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+            const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
             if (I.skip) continue;
             const PairMeta &pm = P.meta[I.p];
             // this row's relabelling: the tile's row, or the listed one (gathered pass)
@@ -657,19 +667,21 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             const bool valid = idx < I.nrow;
             const int64_t b = !valid ? 0 : I.mode == MODE_GATHER ? (int64_t)P.glist[pm.g_off + idx] : idx;
             const uint32_t *lab = P.bits + pm.lab_off + b;
-            // this warp's label word of K-chunk kc (identical for every column tile)
-            auto word = [&](int kc) {
-                const int w0 = 2 * kc + half;
+            // this warp's label word of 64-token atom q of the pair (identical for every
+            // column tile)
+            const int QA = I.KC * AT;  // atoms of a column tile
+            auto word = [&](int q) {
+                const int w0 = 2 * q + half;
                 return valid && w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
             };
-            // loads run MX_PF stages ahead of the expansion (a register ring,
-            // wrapping across column tiles), which covers the DRAM latency
+            // loads run MX_PF atoms ahead of the expansion (a register ring, wrapping
+            // across column tiles), which covers the DRAM latency
             uint32_t rw[MX_PF];
-            int knext = 0;  // K-chunk of the next load
+            int knext = 0;  // atom of the next load
 #pragma unroll
             for (int i = 0; i < MX_PF; ++i) {
                 rw[i] = word(knext);
-                if (++knext == I.KC) knext = 0;
+                if (++knext == QA) knext = 0;
             }
             for (int c = 0; c < I.C && ok; ++c) {
                 for (int kc = 0; kc < I.KC; ++kc) {
@@ -678,23 +690,26 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         ok = false;
                         break;
                     }
-                    uint8_t *row = smem + stage * STAGE + r * 128;
-                    const uint32_t wd = rw[0];
 #pragma unroll
-                    for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
-                    rw[MX_PF - 1] = word(knext);
+                    for (int a = 0; a < AT; ++a) {
+                        uint8_t *row = smem + stage * STAGE + a * MX_A_BYTES + r * 128;
+                        const uint32_t wd = rw[0];
 #pragma unroll
-                    for (int cl = 0; cl < 4; ++cl) {
-                        const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
-                        const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
-                        uint4 v;
-                        v.x = expand2(b8);
-                        v.y = expand2(b8 >> 2);
-                        v.z = expand2(b8 >> 4);
-                        v.w = expand2(b8 >> 6);
-                        *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
+                        for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
+                        rw[MX_PF - 1] = word(knext);
+                        if (++knext == QA) knext = 0;
+#pragma unroll
+                        for (int cl = 0; cl < 4; ++cl) {
+                            const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
+                            const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
+                            uint4 v;
+                            v.x = expand2(b8);
+                            v.y = expand2(b8 >> 2);
+                            v.z = expand2(b8 >> 4);
+                            v.w = expand2(b8 >> 6);
+                            *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
+                        }
                     }
-                    if (++knext == I.KC) knext = 0;
                     fence_proxy_async_smem();
                     __syncwarp();
                     // test hook: CTA 0's first producer warp withholds its first arrival, so
@@ -721,7 +736,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         // across tiles and one final rounding to FP32
         const float chain = 29.0f;
         for (int it = cid; it < n_work && ok; it += ncl) {
-            const ItemInfo I = item_info<DT>(P, P.items[it], CL, sub);
+            const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
             if (I.skip) continue;
             const int p = I.p;
             const PairMeta &pm = P.meta[p];
