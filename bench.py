@@ -34,12 +34,12 @@ METRIC = "perm-tests/sec (B=9999, d=768) vs plain FP32 GPU at exact p-count; % r
 UNIT = "pair-tests/s"
 # DRAM bytes (read + write) of the group-sum GEMM launches of one test call per
 # input token of this workload (B = 9999, d = 768), from the ncu capture of the
-# 256-pair case (238,932 tokens: 1,100,918,272 bytes over the call's four
-# launches; profiles/k_mixed_traffic_batched256_d768.md).  Traffic grows with
-# the tokens, so a call moves this figure x sum(N).  It describes the kernel
-# source it was measured on: another hb_mixed.cu reports null until it is
-# captured again.
-MIXED_TRAFFIC = {"source_sha256_prefix": "3e10a1d776ce7b9b", "bytes_per_token": 1100292096.0 / 238932}
+# 256-pair case (238,932 tokens: 1,332,716,544 bytes over the call's four
+# single-slice launches and its gathered launch;
+# profiles/k_mixed_traffic_batched256_d768.md).  Traffic grows with the tokens,
+# so a call moves this figure x sum(N).  It describes the kernel source it was
+# measured on: another hb_mixed.cu reports null until it is captured again.
+MIXED_TRAFFIC = {"source_sha256_prefix": "59fe2c5f24b6b509", "bytes_per_token": 1332716544.0 / 238932}
 WORKLOAD = ("batched: 4096 word pairs, n and m lognormal (median 300, sigma_log 1.0, clipped 20..8000), d=768 "
             "BF16, half null (sigma 0.35, random directions) / half alternative (sigma ratio 1.1), B=9999 each, "
             "Householder-aligned, two-sided log-volume statistic")

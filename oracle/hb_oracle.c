@@ -44,9 +44,15 @@
  *    floor(w_i * (N - i) / 2^32) < n - (ones so far).  Exactly n ones.
  *  - Exceedance: two-sided |T_b| >= |T_obs| by default (ties count, Eq.
  *    pvalue uses >=); one-sided ">=" and "<=" are selectable.  For the
- *    log-volume statistic the comparison of logarithms is evaluated without
- *    logarithms by cross-multiplying the positive g values, which is exactly
- *    equivalent for positive reals and uses only correctly-rounded IEEE ops.
+ *    log-volume statistic the decision is DEFINED by cross-multiplying the
+ *    positive g values (g2_b * g1_o >= g2_o * g1_b for T_b >= T_obs, and the
+ *    larger-times-smaller form for |T|), each product rounded once in FP64.
+ *    In exact arithmetic this equals comparing the logarithms; with the two
+ *    rounded products it can differ from a comparison of rounded logarithms
+ *    only when the two sides agree to about one ulp, and it keeps structural
+ *    ties (the complement split of n = m, where the products are equal
+ *    exactly) and uses only correctly-rounded IEEE operations, so every
+ *    implementation that follows it reaches the same decision.
  */
 #include <math.h>
 #include <stdint.h>

@@ -96,10 +96,18 @@ __global__ void __launch_bounds__(256) k_recheck_rows(const PairMeta *__restrict
     const int lane = threadIdx.x & 31;
     const int h = (int)threadIdx.x >= G ? 1 : 0, gg = (int)threadIdx.x - h * G;
     const bool live = gg < G;  // blockDim.x may exceed 2G (whole warps)
-    WinAcc wa[8];
+    // exact sums: each value splits into h on the 2^-12 grid and l = v - h on the 2^-28
+    // grid, summed in FP32 (exact for up to 128 values of |v| < 16), folded into 128-bit
+    // totals every 128 values; values below 2^-21 go to the 128-bit total directly
+    // (|v| < 2^-64 counts as 0)
+    const float M = 3072.0f;  // (v + M) - M rounds v to the 2^-12 grid
+    float sh[8], sl[8];
+    i128 tot[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e)
-        wa[e].init(live ? col_bound_exp(colmax[(int64_t)item.pair * o.d_pad + 8 * gg + e]) : 0);
+    for (int e = 0; e < 8; ++e) {
+        sh[e] = sl[e] = 0.0f;
+        tot[e] = 0;
+    }
     int cnt = 0;
     for (int w0 = 0; w0 < pm.W; w0 += RC_WIN_WORDS) {
         const int nw = min(RC_WIN_WORDS, pm.W - w0);
@@ -138,17 +146,31 @@ __global__ void __launch_bounds__(256) k_recheck_rows(const PairMeta *__restrict
             for (int k = 0; k < 4; ++k) {
                 const uint32_t wv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
 #pragma unroll
-                for (int e = 0; e < 8; ++e) wa[e].add((e & 1) ? (wv[e >> 1] & 0xffff0000u) : (wv[e >> 1] << 16));
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t b = (e & 1) ? (wv[e >> 1] & 0xffff0000u) : (wv[e >> 1] << 16);
+                    float x = __uint_as_float(b);
+                    if ((b & 0x7fffffffu) - 1u < (106u << 23) - 1u) {  // 0 < |v| < 2^-21: rare
+                        tot[e] += fixed_from_f32bits(b);
+                        x = 0.0f;
+                    }
+                    const float h = __fsub_rn(__fadd_rn(x, M), M);
+                    sh[e] = __fadd_rn(sh[e], h);
+                    sl[e] = __fadd_rn(sl[e], __fsub_rn(x, h));
+                }
             }
-            if ((++cnt & 31) == 0) {  // at least every 128 adds
+            if ((++cnt & 31) == 0) {  // every 128 values per column
 #pragma unroll
-                for (int e = 0; e < 8; ++e) wa[e].flush();
+                for (int e = 0; e < 8; ++e) {
+                    tot[e] += fixed_from_f32bits(__float_as_uint(sh[e])) + fixed_from_f32bits(__float_as_uint(sl[e]));
+                    sh[e] = sl[e] = 0.0f;
+                }
             }
         }
     }
     i128 acc[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] = wa[e].total();
+    for (int e = 0; e < 8; ++e)
+        acc[e] = tot[e] + fixed_from_f32bits(__float_as_uint(sh[e])) + fixed_from_f32bits(__float_as_uint(sl[e]));
     if (live && h == 1) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) half1[gg * 8 + e] = acc[e];
