@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--d", type=int, default=768)
     ap.add_argument("--path", choices=["mixed", "mixed-2sm", "plain"], default="mixed-2sm")
     ap.add_argument("--s1-max", type=int, default=65536, help="pairs with n + m up to this start with one slice")
+    ap.add_argument("--a-tmem", action="store_true", help="CTA pairs keep the label operand in tensor memory")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -100,8 +101,16 @@ class Clocks:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.25)
+        # never block on the sampler: a stuck nvidia-smi is killed, then abandoned
         self.proc.terminate()
-        self.proc.wait()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                pass
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -431,6 +440,7 @@ def main():
     ctx = H.Context(local)
     H.set_timing(ctx, True)
     H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, a.s1_max)
+    H.set_option(ctx, H.HB_OPT_A_OPERAND_TMEM, 1 if a.a_tmem else 0)
     opts = H.make_opts(B=a.B, seed=1, path=path)
 
     def barrier():
@@ -474,7 +484,7 @@ def main():
     achieved = algo_flops / (gemm_ms / 1000.0) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", 1700.0))
     traffic = None
-    if path == H.HB_PATH_MIXED_2SM and a.B == 9999 and a.d == 768:
+    if path == H.HB_PATH_MIXED_2SM and a.B == 9999 and a.d == 768 and not a.a_tmem:
         import hashlib
 
         src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2605_08048_gb300", "csrc", "hb_mixed.cu")
@@ -565,6 +575,7 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs": P, "B": a.B, "d": a.d, "path": a.path,
+                   "label_operand": "tmem" if a.a_tmem else "smem",
                    "l2": "inputs (%.1f GB) larger than L2; no flush needed" % (XYh.numel() * 2 / 1e9),
                    "sum_tokens": int(np.sum(n + m))},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -359,10 +359,17 @@ hb_status hb_ctx_stage_times(hb_ctx *ctx, float *ms_out, int32_t *n_launches);
  *                               its first GEMM launch, so that a bounded wait
  *                               runs out and the call returns HB_ERR_TIMEOUT
  *                               (the hook then clears itself; plans ignore it)
+ *   HB_OPT_A_OPERAND_TMEM       1 = CTA pairs on BF16 input keep the label
+ *                               operand of the group-sum GEMM in tensor memory
+ *                               (written by the producer warps with tcgen05.st;
+ *                               192-column accumulator tiles) instead of shared
+ *                               memory (256-column tiles; default 0, faster on
+ *                               the batched workload)
  * Options apply to later calls and plans created later. */
 #define HB_OPT_WAIT_LIMIT_NS 1
 #define HB_OPT_SINGLE_SLICE_MAX_N 2
 #define HB_OPT_TEST_WITHHOLD_ARRIVAL 4
+#define HB_OPT_A_OPERAND_TMEM 8
 hb_status hb_ctx_set_option(hb_ctx *ctx, int32_t option, int64_t value);
 
 /* Message of the last failing call on this thread ("" if none). */

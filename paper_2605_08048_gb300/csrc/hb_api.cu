@@ -96,6 +96,7 @@ struct hb_ctx {
     uint64_t wait_ns = 4000000000ull;  // limit of every device barrier wait
     int32_t s1_max = 65536;            // BF16: pairs with n + m <= s1_max start with the single-slice pass
     int32_t withhold = 0;              // test hook: the next tensor-core call withholds one barrier arrival
+    int32_t a_tmem = 0;                // CTA pairs on BF16: the A operand in TMEM
 };
 
 extern "C" void hb_ctx_destroy(hb_ctx *c);
@@ -245,6 +246,7 @@ struct CtxOpts {
     uint64_t wait_ns = 4000000000ull;
     int32_t s1_max = 65536;
     int32_t withhold = 0;
+    int32_t a_tmem = 0;
 };
 
 static CtxOpts ctx_opts(const hb_ctx *c)
@@ -253,6 +255,7 @@ static CtxOpts ctx_opts(const hb_ctx *c)
     k.wait_ns = c->wait_ns;
     k.s1_max = c->s1_max;
     k.withhold = c->withhold;
+    k.a_tmem = c->a_tmem;
     return k;
 }
 
@@ -368,7 +371,10 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         // accumulator tiles of nacc columns: BF16 two grid slices of cw columns (the
         // single-slice pass covers 2 cw columns per tile), FP32 three fixed-point slices
         o.slices = dtype == HB_F32 ? 3 : 2;
-        o.cw = (o.slices == 2 ? 128 : 64) >> (narrow ? 1 : 0);
+        // (CTA pairs on BF16 with the A operand in TMEM: 96, so that the two
+        // 192-column accumulators leave TMEM room for it)
+        o.am = o.slices == 2 && two_sm && k.a_tmem ? 1 : 0;
+        o.cw = o.am ? 96 : (o.slices == 2 ? 128 : 64) >> (narrow ? 1 : 0);
         o.nacc = o.slices * o.cw;
         o.d_pad = (int)rup(d, dtype == HB_F32 ? o.cw : 2 * o.cw);
         o.s1_max = dtype == HB_F32 ? 0 : k.s1_max;
@@ -1569,6 +1575,9 @@ extern "C" hb_status hb_ctx_set_option(hb_ctx *c, int32_t option, int64_t value)
         break;
     case HB_OPT_TEST_WITHHOLD_ARRIVAL:
         c->withhold = value != 0;
+        break;
+    case HB_OPT_A_OPERAND_TMEM:
+        c->a_tmem = value != 0;
         break;
     default:
         return fail(HB_ERR_INVALID_ARG, "option %d unknown", option);

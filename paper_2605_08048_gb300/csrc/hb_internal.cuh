@@ -74,10 +74,11 @@ struct RunOpts {
     int32_t stat, alt, align, reflect_side, exhaustive, path;
     int32_t d, d_pad, dtype, slices;
     int32_t want_T;
-    int32_t cw;      // z-columns per tensor-core tile of all slices (128 BF16, 64 FP32; half when narrow)
+    int32_t cw;      // z-columns per tensor-core tile of one slice (128 BF16, 64 FP32; half when narrow; 96 with am)
     int32_t cg;      // tensor-core path: 1 = one CTA per MMA, 2 = CTA pairs (M = 256)
     int32_t nacc;    // accumulator columns of a tensor-core tile: slices * cw
     int32_t s1_max;  // BF16 tensor-core path: pairs with N <= s1_max take the single-slice pass first
+    int32_t am;      // BF16 on CTA pairs: the A operand in TMEM (192-column accumulators) instead of shared memory
 };
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,7 @@ constexpr int MX_K = 64;             // tokens of one 128-byte swizzle atom of B
 constexpr int MX_PF = 6;             // label-word prefetch distance of the A producers (stages)
 constexpr int MX_A_BYTES = MX_M * MX_K * 2;       // 16 KB: the A tile of one atom
 constexpr int MX_NACC = 256;         // accumulator columns of one TMEM buffer
+constexpr int MX_NACC_TA = 192;      // the same with the A operand in TMEM (CTA pairs, BF16)
 constexpr int MX_BOXR_MIN = 32;      // slice rows per TMA box: at least this, at most 128
 constexpr int MX_APROD = 8;          // A-producer warps (two per row block, one label word each)
 constexpr int MX_THREADS = 192 + 32 * MX_APROD;
@@ -77,8 +78,8 @@ static_assert(MX_BOUND_THREADS >= MX_THREADS, "launch bound");
 constexpr int MX_TMEM_COLS = 512;    // two accumulator buffers of MX_NACC columns
 constexpr int MX_STAGE_AREA = 192 * 1024;  // CG = 1: 4 stages of 48 KB; CG = 2: 6 of 32 KB
 constexpr int MX_BAR_OFF = MX_STAGE_AREA;
-constexpr int MX_CONST_OFF = MX_BAR_OFF + 256;
-constexpr int MX_SMEM = 1024 + MX_CONST_OFF + 4 * MX_NACC * 8;  // per-epilogue-warp column constants
+constexpr int MX_CONST_OFF = MX_BAR_OFF + 512;
+constexpr int MX_SMEM = 1024 + MX_CONST_OFF + 4 * 4 * MX_NACC * 4;  // per epilogue warp: two tiles' t and q_hi
 
 struct MixedParams {
     const PairMeta *meta;
@@ -197,6 +198,15 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
+// arrive on an mbarrier of another CTA without a release: for signals that
+// publish no memory writes (TMEM stores the thread has waited for, ordered by
+// tcgen05.fence::before_thread_sync), where a cluster-scope release would cost
+// about a microsecond
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -251,6 +261,15 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async), and its groups
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -295,6 +314,20 @@ __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, 
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T across the CTA pair: as umma_bf16_pair,
+// with each CTA's 128 rows of A in its own TMEM (row = lane, two BF16 values
+// of consecutive k per 32-bit column, the lower k in the low half).
+__device__ __forceinline__ void umma_bf16_pair_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                  uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -349,6 +382,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive TMEM columns of this thread's lane from 16 registers
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row core groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -368,10 +413,63 @@ __host__ __device__ __forceinline__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// two labels (bits 0, 1 of b) -> two BF16 values 0.0 / 1.0 packed in 32 bits
-__device__ __forceinline__ uint32_t expand2(uint32_t b)
+
+// Packed FP32 pairs (f32x2): two independent IEEE single-precision
+// operations, round to nearest, in one instruction; the low word is the
+// first element.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b)
 {
-    return ((b & 1u) ? 0x3F80u : 0u) | ((b & 2u) ? 0x3F800000u : 0u);
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// The even-indexed bits of w to bits 0..15 and the odd-indexed ones to bits
+// 16..31, in order (four delta swaps: 2 <-> 1 within nibbles, then 2-bit,
+// nibble and byte fields).
+__device__ __forceinline__ uint32_t unshuffle32(uint32_t x)
+{
+    uint32_t t;
+    t = (x ^ (x >> 1)) & 0x22222222u;
+    x ^= t ^ (t << 1);
+    t = (x ^ (x >> 2)) & 0x0C0C0C0Cu;
+    x ^= t ^ (t << 2);
+    t = (x ^ (x >> 4)) & 0x00F000F0u;
+    x ^= t ^ (t << 4);
+    t = (x ^ (x >> 8)) & 0x0000FF00u;
+    x ^= t ^ (t << 8);
+    return x;
+}
+
+// One label word (32 tokens) -> 16 words of two BF16 labels 0.0 / 1.0: word j
+// holds tokens 2j (low half) and 2j + 1 (high half).  After unshuffle32,
+// word j is bits j and 16 + j of x times 0x3F80 (BF16 1.0) in each half; as
+// 0x3F80 = 127 * 2^7, for j < 8 the shift folds into the multiplier.
+__device__ __forceinline__ void expand_word(uint32_t w, uint32_t (&v)[16])
+{
+    const uint32_t x = unshuffle32(w), x8 = x >> 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        v[j] = (x & (0x00010001u << j)) * (0x3F80u >> j);
+        v[j + 8] = (x8 & (0x00010001u << j)) * (0x3F80u >> j);
+    }
 }
 
 // What every role of a CTA needs to know about one work item; every role
@@ -410,21 +508,30 @@ __device__ __forceinline__ ItemInfo item_info(const MixedParams &P, const WorkIt
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int CG, int DT>
+template <int CG, int DT, int AM>
 __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_constant__ CUtensorMap tmap, const MixedParams P)
 {
+    static_assert(AM == 0 || (CG == 2 && DT == DT_BF16), "A in TMEM: CTA pairs on BF16 slices");
     constexpr int CL = CG;  // CTAs per work item (a cluster of two for CTA pairs)
     // stages: AT swizzle atoms of 64 tokens, each an A tile (16 KB) and this CTA's
     // B rows (up to 256 x 128 B for single CTAs, 128 x 128 B for CTA pairs).  CTA
     // pairs take two atoms per stage (eight MMAs per barrier handshake, which halves
     // the handshakes' cost) in three stages of 64 KB; single CTAs one atom in four
     // stages of 48 KB
+    // With the A operand in TMEM (AM = 1: CTA pairs, 192 accumulator columns)
+    // shared memory holds only the B halves, 2 x 96 rows x 128 B a stage, in
+    // eight stages; the A tiles of four 64-token atoms sit in TMEM columns
+    // 384..511 behind the two accumulator buffers.
     constexpr int AT = CG == 2 ? 2 : 1;
     constexpr int KS = AT * MX_K;                  // tokens per stage
-    constexpr int A_BYTES = AT * MX_A_BYTES;
-    constexpr int STAGE = CG == 2 ? 64 * 1024 : 48 * 1024;
-    constexpr int NS = CG == 2 ? 3 : 4;
+    constexpr int A_BYTES = AM ? 0 : AT * MX_A_BYTES;
+    constexpr int STAGE = AM ? 24 * 1024 : (CG == 2 ? 64 * 1024 : 48 * 1024);
+    constexpr int NS = AM ? 8 : (CG == 2 ? 3 : 4);
+    constexpr int NSA = 4;                                   // AM: A stages (one atom each) in TMEM
+    constexpr uint32_t ACCS = AM ? MX_NACC_TA : MX_NACC;     // TMEM columns of one accumulator buffer
+    constexpr uint32_t ACOL = 2 * ACCS;                      // AM: TMEM column of A stage 0
     static_assert(NS * STAGE <= MX_STAGE_AREA, "stage layout");
+    static_assert(!AM || ACOL + NSA * (MX_K / 2) <= MX_TMEM_COLS, "TMEM columns");
     // CG = 2: the odd CTA reports its A stages to the even one in groups of RG
     // stages; the even CTA waits at the first stage of each group
     constexpr int RG = 1;
@@ -444,7 +551,11 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     const uint32_t drain = bar0 + 8u * (3 * NS + 4);
     // CG = 2, even CTA: the odd CTA's A tiles of stages s .. s + RG - 1 are in place
     auto peer_ready = [&](int s) { return bar0 + 8u * (3 * NS + 5 + s); };
-    static_assert(8 * (4 * NS + 5) + 4 <= 256, "barrier block");
+    // AM: A stage sa is in TMEM (every producer warp of both CTAs has arrived;
+    // on the even CTA) / free again (the MMAs reading it completed; both CTAs)
+    auto afull = [&](int sa) { return bar0 + 8u * (NS + sa); };
+    auto aempty = [&](int sa) { return peer_ready(sa); };
+    static_assert(8 * (4 * NS + 5) + 4 <= MX_CONST_OFF - MX_BAR_OFF, "barrier block");
     uint32_t *tmem_holder = (uint32_t *)(smem + MX_BAR_OFF + 8 * (4 * NS + 5));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -460,9 +571,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(full(s), MX_APROD + (leader ? 1 : 0));
+            mbar_init(full(s), AM ? 1 : MX_APROD + (leader ? 1 : 0));
             mbar_init(empty(s), 1);  // the MMA commit (CG = 2: the pair's commit reaches both CTAs)
-            mbar_init(peer_ready(s), 1);
+            mbar_init(peer_ready(s), 1);  // AM: aempty
+            if (AM && s < NSA) mbar_init(afull(s), 2 * MX_APROD);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
@@ -556,8 +668,9 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         }
     } else if (warp == 5 && !leader) {
         // ---------------- CG = 2, odd CTA: tells the even CTA when its A tiles are in ----------------
-        // (its B halves are counted on the even CTA's barriers by the copies themselves)
-        if (lane == 0) {
+        // (its B halves are counted on the even CTA's barriers by the copies themselves;
+        // with A in TMEM the producers arrive on the even CTA's barriers directly)
+        if (!AM && lane == 0) {
             const uint32_t rank0 = crank - 1u;
             int stage = 0;
             uint32_t phase = 0;
@@ -586,6 +699,72 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             }
             // the last group may be short: its stages are all in
             if (ok && pending >= 0) mbar_arrive_remote(mapa_rank(peer_ready(pending), rank0));
+        }
+    } else if (warp == 5 && AM) {
+        // ---------------- MMA issuer, A in TMEM ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(MX_M * CG, nacc);
+            const uint32_t dhi = (uint32_t)(sw128_desc(sbase) >> 32);
+            const uint32_t blo0 = (uint32_t)sw128_desc(sbase);
+            constexpr uint32_t STEP = STAGE >> 4;
+            const uint32_t BAOFF = (uint32_t)(nacc / CG) * 8u;  // one atom of this CTA's B rows, 16-byte units
+            int stage = 0, sa = 0, abuf = 0;
+            uint32_t phase = 0, aph = 0, aphase = 0, blo = blo0;
+            bool ok = true;
+            for (int it = cid; it < n_work && ok; it += ncl) {
+                const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
+                if (I.skip) continue;
+                for (int c = 0; c < I.C && ok; ++c) {
+                    if (!mbar_wait(acc_empty(abuf), aphase ^ 1u, P.timeout, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem + (uint32_t)abuf * ACCS;
+                    for (int kc = 0; kc < I.KC && ok; ++kc) {
+                        if (!mbar_wait(full(stage), phase, P.timeout, lim)) {
+                            ok = false;
+                            break;
+                        }
+#pragma unroll
+                        for (int a = 0; a < AT; ++a) {
+                            // both CTAs' A tiles of this atom (the odd CTA's producers arrive once
+                            // their TMEM stores are complete; the fence below orders the MMAs after)
+                            if (!mbar_wait(afull(sa), aph, P.timeout, lim)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t at = tmem + ACOL + (uint32_t)sa * (MX_K / 2);
+#pragma unroll
+                            for (int kk = 0; kk < MX_K / 16; ++kk) {
+                                const uint64_t bd = ((uint64_t)dhi << 32) | (blo + a * BAOFF + 2u * kk);
+                                umma_bf16_pair_ta(dt, at + 8u * kk, bd, idesc, (kc | a | kk) != 0 ? 1u : 0u);
+                            }
+                            umma_commit_pair_mc(aempty(sa), pair_mask);  // this A stage is free in both CTAs
+                            if (++sa == NSA) {
+                                sa = 0;
+                                aph ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        umma_commit_pair_mc(empty(stage), pair_mask);  // this B stage is free in both CTAs
+                        blo += STEP;
+                        if (++stage == NS) {
+                            stage = 0;
+                            phase ^= 1u;
+                            blo = blo0;
+                        }
+                    }
+                    if (!ok) break;
+                    umma_commit_pair_mc(acc_full(abuf), pair_mask);  // both CTAs' epilogues
+                    abuf ^= 1;
+                    if (abuf == 0) aphase ^= 1u;
+                }
+            }
+            umma_commit_pair_mc(drain, (uint16_t)(1u << crank));
+            unsigned int dummy = 0;
+            mbar_wait(drain, 0, ok ? P.timeout : &dummy, lim);
         }
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
@@ -652,8 +831,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     } else if (warp >= 6) {
         // ---------------- A producers: label bits -> BF16 0/1 ----------------
         const int pi = warp - 6;
-        const int r = (pi & 3) * 32 + lane;  // relabelling row of the tile, 0..127
-        const int half = pi >> 2;            // the 32-token half of each stage this warp fills
+        // relabelling row of the tile, 0..127 (AM: the TMEM lane quarter this warp may
+        // access is warp % 4)
+        const int r = AM ? (warp & 3) * 32 + lane : (pi & 3) * 32 + lane;
+        const int half = pi >> 2;            // the 32-token half of each atom this warp fills
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -667,12 +848,14 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             const bool valid = idx < I.nrow;
             const int64_t b = !valid ? 0 : I.mode == MODE_GATHER ? (int64_t)P.glist[pm.g_off + idx] : idx;
             const uint32_t *lab = P.bits + pm.lab_off + b;
+            const int nW = pm.W;             // (in registers: the asm statements below clobber memory)
+            const int64_t nBp = pm.B_pad;
             // this warp's label word of 64-token atom q of the pair (identical for every
             // column tile)
             const int QA = I.KC * AT;  // atoms of a column tile
             auto word = [&](int q) {
                 const int w0 = 2 * q + half;
-                return valid && w0 < pm.W ? __ldg(lab + (int64_t)w0 * pm.B_pad) : 0u;
+                return valid && w0 < nW ? __ldg(lab + (int64_t)w0 * nBp) : 0u;
             };
             // loads run MX_PF atoms ahead of the expansion (a register ring, wrapping
             // across column tiles), which covers the DRAM latency
@@ -682,6 +865,42 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             for (int i = 0; i < MX_PF; ++i) {
                 rw[i] = word(knext);
                 if (++knext == QA) knext = 0;
+            }
+            if (AM) {
+                // one atom per A stage: this warp's label word of the atom, expanded to 16
+                // TMEM columns of two BF16 labels (tokens 2j, 2j + 1 of the word in column j)
+                const uint32_t trow = tmem + ((uint32_t)(r & ~31) << 16) + ACOL + (uint32_t)half * 16u;
+                for (int q = 0; q < I.C * QA && ok; ++q) {
+                    // the MMAs that read this stage are complete (their commit flipped the
+                    // barrier): the stores below cannot overtake them, so no
+                    // tcgen05.fence::after_thread_sync is needed (it costs about 200
+                    // clocks here)
+                    if (!warp_wait(aempty(stage), phase ^ 1u, P.timeout, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    uint32_t v[16];
+                    expand_word(rw[0], v);
+#pragma unroll
+                    for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
+                    rw[MX_PF - 1] = word(knext);
+                    if (++knext == QA) knext = 0;
+                    tmem_st16(trow + (uint32_t)stage * (MX_K / 2), v);
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    const bool hold = P.withhold && !withheld && blockIdx.x == 0 && pi == 0;
+                    withheld |= hold;
+                    if (lane == 0 && !hold) {
+                        if (leader) mbar_arrive(afull(stage));
+                        else mbar_arrive_remote_relaxed(mapa_rank(afull(stage), crank - 1u));
+                    }
+                    if (++stage == NSA) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                continue;
             }
             for (int c = 0; c < I.C && ok; ++c) {
                 for (int kc = 0; kc < I.KC; ++kc) {
@@ -698,16 +917,13 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
                         rw[MX_PF - 1] = word(knext);
                         if (++knext == QA) knext = 0;
+                        uint32_t v[16];
+                        expand_word(wd, v);
 #pragma unroll
                         for (int cl = 0; cl < 4; ++cl) {
                             const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens
-                            const uint32_t b8 = (wd >> (cl * 8)) & 0xffu;
-                            uint4 v;
-                            v.x = expand2(b8);
-                            v.y = expand2(b8 >> 2);
-                            v.z = expand2(b8 >> 4);
-                            v.w = expand2(b8 >> 6);
-                            *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) = v;
+                            *(uint4 *)(row + ((ch ^ (r & 7)) << 4)) =
+                                make_uint4(v[4 * cl], v[4 * cl + 1], v[4 * cl + 2], v[4 * cl + 3]);
                         }
                     }
                     fence_proxy_async_smem();
@@ -727,42 +943,68 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     } else {
         // ---------------- epilogue (warps 0-3 = TMEM lanes 0-127) ----------------
         const int r = threadIdx.x;  // TMEM lane = relabelling row
-        float2 *consts = (float2 *)(smem + MX_CONST_OFF) + warp * MX_NACC;
-        int abuf = 0;
+        // this warp's column constants (totals t and, FP32 storage, slice scales
+        // q_hi) of two tiles: the current one and the next, fetched by cp.async
+        // while the current one is waited for and consumed
+        float *const cbase = (float *)(smem + MX_CONST_OFF) + warp * 4 * MX_NACC;
+        auto fetch = [&](int p, int c, int cw, int buf) {
+            float *t = cbase + buf * 2 * MX_NACC;
+            for (int jj = lane; jj < cw; jj += 32) {
+                const int j = c * cw + jj;
+                if (j < o.d) {
+                    const ColConst *q = P.cc + (int64_t)p * o.d_pad + j;
+                    cp_async4(t + jj, &q->t);
+                    if (DT == DT_F32) cp_async4(t + MX_NACC + jj, &q->q_hi);
+                } else {
+                    t[jj] = 0.f;  // columns past d
+                    t[MX_NACC + jj] = 0.f;
+                }
+            }
+            cp_async_commit();
+        };
+        auto next_item = [&](int from, ItemInfo &J) {
+            for (int k = from; k < n_work; k += ncl) {
+                J = item_info<DT, KS>(P, P.items[k], CL, sub);
+                if (!J.skip) return k;
+            }
+            return n_work;
+        };
+        int abuf = 0, cb = 0;
         uint32_t aphase = 0;
         bool ok = true;
         // rounding chain of each squared norm: 4 FMAs per interleaved accumulator,
         // 2 combining adds, up to 16 chunk adds per tile, then exact-enough FP64
         // across tiles and one final rounding to FP32
         const float chain = 29.0f;
-        for (int it = cid; it < n_work && ok; it += ncl) {
-            const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
-            if (I.skip) continue;
+        ItemInfo I;
+        int it = next_item(cid, I);
+        if (it < n_work) fetch(I.p, 0, I.cw, 0);
+        for (; it < n_work && ok;) {
+            ItemInfo NI;
+            const int nit = next_item(it + ncl, NI);
             const int p = I.p;
             const PairMeta &pm = P.meta[p];
             const bool single = I.mode == MODE_SINGLE;
             const int nch = I.cw / 16;
             double Q1 = 0.0, Q2 = 0.0;
             for (int c = 0; c < I.C; ++c) {
-                // this warp's copy of the tile's column constants (scale, total; no
-                // cross-warp barrier); columns past d hold zeros
+                // every lane is done with the other buffer (the previous tile): fetch the
+                // next tile's constants into it, then wait for this tile's (all copy
+                // groups but the newest; an empty group keeps the count uniform)
                 __syncwarp();
-                for (int jj = lane; jj < I.cw; jj += 32) {
-                    const int j = c * I.cw + jj;
-                    float2 k = make_float2(0.f, 0.f);
-                    if (j < o.d) {
-                        const ColConst q = P.cc[(int64_t)p * o.d_pad + j];
-                        k = make_float2(q.q_hi, q.t);
-                    }
-                    consts[jj] = k;
-                }
+                if (c + 1 < I.C) fetch(p, c + 1, I.cw, cb ^ 1);
+                else if (nit < n_work) fetch(NI.p, 0, NI.cw, cb ^ 1);
+                else cp_async_commit();
+                cp_async_wait1();
                 __syncwarp();
+                const float *tt = cbase + cb * 2 * MX_NACC, *qq = tt + MX_NACC;
+                cb ^= 1;
                 if (!warp_wait(acc_full(abuf), aphase, P.timeout, lim)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)abuf * MX_NACC;
+                const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)abuf * ACCS;
                 float pq1[4] = {0.f, 0.f, 0.f, 0.f}, pq2[4] = {0.f, 0.f, 0.f, 0.f};
                 float tq1 = 0.f, tq2 = 0.f;
                 // per column: sigma_1, sigma_2 = t - sigma_1 and both squares; the band's
@@ -782,21 +1024,41 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                 if (DT == DT_BF16 && I.S == 1) {
                     // the single-slice pass (the hot path): the slice holds values, so
                     // sigma_1 = D exactly; the next chunk's TMEM load is in flight while
-                    // this one is consumed
+                    // this one is consumed.  The same operations as `column` and `fold`,
+                    // two columns per instruction: accumulator pair a holds pq[0], pq[1],
+                    // pair b pq[2], pq[3]
+                    f2_t p1a = 0ull, p1b = 0ull, p2a = 0ull, p2b = 0ull;
+                    auto chunk = [&](const uint32_t (&dv)[16], int c0) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4) {
+                            const float4 t4 = *(const float4 *)(tt + c0 + i);
+                            const f2_t sa = f2_pack(__uint_as_float(dv[i]), __uint_as_float(dv[i + 1]));
+                            const f2_t sb = f2_pack(__uint_as_float(dv[i + 2]), __uint_as_float(dv[i + 3]));
+                            const f2_t ra = f2_sub(f2_pack(t4.x, t4.y), sa), rb = f2_sub(f2_pack(t4.z, t4.w), sb);
+                            p1a = f2_fma(sa, sa, p1a);
+                            p1b = f2_fma(sb, sb, p1b);
+                            p2a = f2_fma(ra, ra, p2a);
+                            p2b = f2_fma(rb, rb, p2b);
+                        }
+                        float x0, x1, x2, x3;
+                        f2_unpack(p1a, x0, x1);
+                        f2_unpack(p1b, x2, x3);
+                        tq1 += (x0 + x1) + (x2 + x3);
+                        f2_unpack(p2a, x0, x1);
+                        f2_unpack(p2b, x2, x3);
+                        tq2 += (x0 + x1) + (x2 + x3);
+                        p1a = p1b = p2a = p2b = 0ull;
+                    };
                     uint32_t da[16], db[16];
                     tmem_ld16(tb, da);
                     tmem_ld_wait();
 #pragma unroll 1
                     for (int ch = 0; ch < nch; ch += 2) {
                         tmem_ld16(tb + (ch + 1) * 16, db);  // nch is even
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) column(i, __uint_as_float(da[i]), consts[ch * 16 + i].y);
-                        fold();
+                        chunk(da, ch * 16);
                         tmem_ld_wait();
                         if (ch + 2 < nch) tmem_ld16(tb + (ch + 2) * 16, da);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) column(i, __uint_as_float(db[i]), consts[(ch + 1) * 16 + i].y);
-                        fold();
+                        chunk(db, (ch + 1) * 16);
                         tmem_ld_wait();
                     }
                 } else {
@@ -812,7 +1074,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         tmem_ld_wait();
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const float2 k = consts[ch * 16 + i];
+                            const float2 k = make_float2(qq[ch * 16 + i], tt[ch * 16 + i]);
                             float s1;
                             if (DT == DT_BF16) {
                                 s1 = __fadd_rn(__uint_as_float(d0[i]), __uint_as_float(d1[i]));
@@ -869,7 +1131,10 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                 if (ex) atomicAdd(&P.st[p].count, (unsigned long long)__popc(ex));
                 atomicMax(&P.st[p].band_max_bits, __float_as_uint(bm));
             }
+            it = nit;
+            I = NI;
         }
+        cp_async_wait0();  // no copy into this CTA's shared memory outlives the loop
     }
 
     // no CTA leaves while a peer may still copy into its shared memory or
@@ -945,10 +1210,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string &err)
 
 typedef void (*MixedKernel)(const CUtensorMap, const MixedParams);
 
-template <int DT>
-static MixedKernel pick_kernel(int cg)
+// am: CTA pairs on BF16 slices with the A operand in TMEM
+static MixedKernel pick_kernel(int dtype, int cg, bool am)
 {
-    return cg == 2 ? k_mixed<2, DT> : k_mixed<1, DT>;
+    if (dtype == DT_BF16) return cg == 2 ? (am ? k_mixed<2, DT_BF16, 1> : k_mixed<2, DT_BF16, 0>) : k_mixed<1, DT_BF16, 0>;
+    return cg == 2 ? k_mixed<2, DT_F32, 0> : k_mixed<1, DT_F32, 0>;
 }
 
 cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
@@ -960,14 +1226,17 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
         return cudaErrorInvalidValue;
     }
     const int CGv = a.o.cg == 2 ? 2 : 1;
-    if (nacc > MX_NACC || nacc % (MX_BOXR_MIN * CGv) != 0 || nacc % S != 0 || (nacc / S) % MX_BOXR_MIN != 0) {
+    const bool am = a.o.am && a.o.dtype == DT_BF16 && CGv == 2;
+    if (nacc > MX_NACC || nacc % (MX_BOXR_MIN * CGv) != 0 || nacc % S != 0 || (nacc / S) % MX_BOXR_MIN != 0 ||
+        (am && nacc != MX_NACC_TA)) {
         err = "unsupported column tile width";
         return cudaErrorInvalidValue;
     }
-    // the largest box that divides both a slice's z-columns of a tile and this
-    // CTA's share of the tile, at most 128 rows (at most 8 boxes per stage)
+    // the largest box (a multiple of 8 rows: whole 1 KB swizzle groups) that divides
+    // both a slice's z-columns of a tile and this CTA's share of the tile, at most
+    // 128 rows (at most 8 boxes per stage)
     int br = 128;
-    while ((nacc / S) % br != 0 || (nacc / CGv) % br != 0) br >>= 1;
+    while ((nacc / S) % br != 0 || (nacc / CGv) % br != 0) br -= 8;
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode(err);
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
@@ -1001,7 +1270,7 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     prm.wait_ns = a.wait_ns;
     prm.withhold = a.withhold;
     prm.box_rows = br;
-    const MixedKernel kern = a.o.dtype == DT_BF16 ? pick_kernel<DT_BF16>(CGv) : pick_kernel<DT_F32>(CGv);
+    const MixedKernel kern = pick_kernel(a.o.dtype, CGv, am);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
     if (e != cudaSuccess) return e;
     const int CL = CGv;

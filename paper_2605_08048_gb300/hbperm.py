@@ -415,7 +415,7 @@ def declared_symbols(header: str | None = None):
     return sorted(set(re.findall(r"^\s*(?:hb_status|void|int64_t|const char \*)\s*(hb_\w+)\s*\(", src, re.M)))
 
 
-HB_OPT_WAIT_LIMIT_NS, HB_OPT_SINGLE_SLICE_MAX_N, HB_OPT_TEST_WITHHOLD_ARRIVAL = 1, 2, 4
+HB_OPT_WAIT_LIMIT_NS, HB_OPT_SINGLE_SLICE_MAX_N, HB_OPT_TEST_WITHHOLD_ARRIVAL, HB_OPT_A_OPERAND_TMEM = 1, 2, 4, 8
 
 
 def set_option(ctx: Context, option: int, value: int):

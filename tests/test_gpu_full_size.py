@@ -100,15 +100,20 @@ def _golden_batched():
     return rows
 
 
-@pytest.mark.parametrize("path", [H.HB_PATH_MIXED_2SM, H.HB_PATH_MIXED])
-def test_batched_full_size_every_pair(ctx, path):
+@pytest.mark.parametrize("path,a_tmem", [(H.HB_PATH_MIXED_2SM, 0), (H.HB_PATH_MIXED, 0), (H.HB_PATH_MIXED_2SM, 1)],
+                         ids=["mixed-2sm", "mixed", "mixed-2sm-tmem"])
+def test_batched_full_size_every_pair(ctx, path, a_tmem):
     """The benchmark's whole workload (4096 pairs, B = 9999, the launch
     configuration the benchmark times) against the oracle's stored results for
     every pair: sizes, status, count and p bit for bit, plus T_obs of a sample
-    recomputed by the oracle."""
+    recomputed by the oracle.  Also with the label operand in tensor memory."""
     rows = _golden_batched()
     b = synth.workload_batched(seed=1237, P=4096)
-    res = H.hb_perm_test_batched(ctx, dev(b.XY), b.n, b.m, H.make_opts(B=9999, seed=1, path=path))
+    H.set_option(ctx, H.HB_OPT_A_OPERAND_TMEM, a_tmem)
+    try:
+        res = H.hb_perm_test_batched(ctx, dev(b.XY), b.n, b.m, H.make_opts(B=9999, seed=1, path=path))
+    finally:
+        H.set_option(ctx, H.HB_OPT_A_OPERAND_TMEM, 0)
     for k, (pi, n, m, st, cnt, p) in enumerate(rows):
         assert int(pi) == k and int(n) == b.n[k] and int(m) == b.m[k]
         assert res[k]["status"] == int(st)

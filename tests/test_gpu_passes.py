@@ -10,7 +10,11 @@ whose band is wide (many relabellings gathered) and switched off.
 Every mbarrier wait of the tensor-core kernels is bounded: with one arrival
 withheld (a test hook; nothing then completes that barrier) the wait runs
 out, the call returns HB_ERR_TIMEOUT, and the next call on the same context
-gives the oracle's results again."""
+gives the oracle's results again.
+
+Every case also runs on CTA pairs with the label operand in tensor memory
+(HB_OPT_A_OPERAND_TMEM: tcgen05.st by the producer warps, 192-column
+accumulator tiles)."""
 import numpy as np
 import pytest
 
@@ -22,8 +26,9 @@ from paper_2605_08048_gb300 import synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-ROUTES = [pytest.param(H.HB_PATH_MIXED, id="mixed"), pytest.param(H.HB_PATH_MIXED_2SM, id="mixed-2sm"),
-          pytest.param(H.HB_PATH_MIXED_NARROW, id="mixed-narrow")]
+ROUTES = [pytest.param((H.HB_PATH_MIXED, 0), id="mixed"), pytest.param((H.HB_PATH_MIXED_2SM, 0), id="mixed-2sm"),
+          pytest.param((H.HB_PATH_MIXED_2SM, 1), id="mixed-2sm-tmem"),
+          pytest.param((H.HB_PATH_MIXED_NARROW, 0), id="mixed-narrow")]
 
 
 def dev(a: np.ndarray):
@@ -39,9 +44,10 @@ def ctx():
     c.close()
 
 
-def _set(ctx, s1_max=65536, wait_ns=4_000_000_000):
+def _set(ctx, s1_max=65536, wait_ns=4_000_000_000, a_tmem=0):
     H.set_option(ctx, H.HB_OPT_SINGLE_SLICE_MAX_N, s1_max)
     H.set_option(ctx, H.HB_OPT_WAIT_LIMIT_NS, wait_ns)
+    H.set_option(ctx, H.HB_OPT_A_OPERAND_TMEM, a_tmem)
 
 
 @pytest.mark.parametrize("route", ROUTES)
@@ -50,8 +56,8 @@ def test_passes_parity_wide_band(ctx, route, s1_max):
     """A null pair of 6000 tokens: its single-slice band is wide, so the
     gathered pass decides many relabellings; counts, p and the statistics of
     every relabelling agree with the oracle."""
-    path = route
-    _set(ctx, s1_max=s1_max)
+    path, tm = route
+    _set(ctx, s1_max=s1_max, a_tmem=tm)
     X, Y = synth.pair(4321, 3100, 2900, 768, 0.35, 0.35, None, "bf16")
     B = 1500
     ref, Tref, _ = O.perm_test(X, Y, O.opts(B=B, seed=9), want_T=True)
@@ -67,8 +73,8 @@ def test_passes_parity_wide_band(ctx, route, s1_max):
 def test_passes_parity_batch_mixed_sizes(ctx, route):
     """Pairs on both sides of the single-slice limit in one batch (limit set
     to 600 tokens), ragged sizes, one degenerate pair."""
-    path = route
-    _set(ctx, s1_max=600)
+    path, tm = route
+    _set(ctx, s1_max=600, a_tmem=tm)
     n = np.array([300, 2, 1, 700, 45, 1000, 260], dtype=np.int64)
     m = np.array([250, 9, 30, 20, 3000, 990, 340], dtype=np.int64)
     b = synth.batch(77, len(n), 256, "bf16", sizes=(n, m))
@@ -83,17 +89,17 @@ def test_passes_parity_batch_mixed_sizes(ctx, route):
 
 @pytest.mark.parametrize("route", ROUTES)
 def test_bounded_wait_timeout_then_recovery(ctx, route):
-    path = route
+    path, tm = route
     X, Y = synth.pair(555, 700, 900, 768, 0.35, 0.385, None, "bf16")
     Xd, Yd = dev(X), dev(Y)
     opts = H.make_opts(B=3000, seed=12, path=path)
-    _set(ctx, wait_ns=50_000_000)
+    _set(ctx, wait_ns=50_000_000, a_tmem=tm)
     H.set_option(ctx, H.HB_OPT_TEST_WITHHOLD_ARRIVAL, 1)
     with pytest.raises(H.HbError) as e:
         H.hb_perm_test(ctx, Xd, Yd, opts)
     assert e.value.status == H.HB_ERR_TIMEOUT
     # the hook acts on one call; the same context then gives the oracle's results
-    _set(ctx)
+    _set(ctx, a_tmem=tm)
     res, _ = H.hb_perm_test(ctx, Xd, Yd, opts)
     ref, _, _ = O.perm_test(X, Y, O.opts(B=3000, seed=12))
     assert res["status"] == 0 and res["count"] == ref["count"] and res["p"] == ref["p"]
