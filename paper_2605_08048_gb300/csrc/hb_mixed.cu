@@ -34,8 +34,8 @@
 //              sigma_2 = t - sigma_1, squared norms, band (its first-order
 //              term by Cauchy-Schwarz from the column bounds' norm), decision
 //   warp  4    TMA producer of the B tiles
-//   warp  5    MMA issuer (one elected lane); with CTA pairs (CG = 2) the odd
-//              CTA's warp 5 relays its A readiness to the even CTA instead
+//   warp  5    MMA issuer (one elected lane; with CTA pairs (CG = 2) the even
+//              CTA's, whose barriers count both CTAs' operands)
 //   warps 6-13 A producers (label bits -> BF16 0/1 tiles): warp 6 + i
 //              expands rows 32*(i%4) .. +31, tokens 32*(i/4) .. +31 (one
 //              label word) of every stage
@@ -45,7 +45,11 @@
 // Variants: CG = 2 (tcgen05 cta_group::2 on CTA pairs, M = 256, each CTA
 // loading half of every B tile: the default route, half the B bytes per SM of
 // single CTAs) and CG = 1 (single CTAs, each loading its own B tiles; also the
-// gathered pass).  No copy is multicast.
+// gathered pass).  No copy is multicast.  AM = 1 (CTA pairs, BF16) keeps the
+// A operand in TMEM instead: the producer warps write it with tcgen05.st
+// (warp w reaches TMEM lanes 32 (w % 4) .. +31) and the accumulator tiles
+// shrink to 192 columns to make room for four 64-token A stages; shared
+// memory then holds only B, in eight stages.
 // Every mbarrier wait is bounded (wall-clock limit, a launch parameter); on
 // expiry the kernel raises the timeout flag, drains its own copies and MMAs,
 // frees TMEM and returns, and the host reports HB_ERR_TIMEOUT.
@@ -152,50 +156,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
-// try_wait with acquire at cluster scope: for barriers a peer CTA arrives on
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0u;
-}
-
-// bounded wait as mbar_wait, with cluster-scope acquire
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, unsigned int *timeout,
-                                                  uint64_t limit_ns)
-{
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait_cluster(bar, parity)) return true;
-        if ((it & 255u) == 0u) {
-            if (*(volatile unsigned int *)timeout) return false;
-            if (globaltimer() - t0 > limit_ns) {
-                atomicExch(timeout, 1u);
-                return false;
-            }
-        }
-    }
-}
-
 // the same shared-memory offset in CTA `rank` of the cluster
 __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
 {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
-}
-
-// arrive, with release at cluster scope, on an mbarrier of another CTA
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 // arrive on an mbarrier of another CTA without a release: for signals that
@@ -532,10 +498,6 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     constexpr uint32_t ACOL = 2 * ACCS;                      // AM: TMEM column of A stage 0
     static_assert(NS * STAGE <= MX_STAGE_AREA, "stage layout");
     static_assert(!AM || ACOL + NSA * (MX_K / 2) <= MX_TMEM_COLS, "TMEM columns");
-    // CG = 2: the odd CTA reports its A stages to the even one in groups of RG
-    // stages; the even CTA waits at the first stage of each group
-    constexpr int RG = 1;
-    static_assert(NS % RG == 0 && NS >= 2 * RG, "relay groups");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -543,18 +505,17 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
     const uint32_t bar0 = sbase + MX_BAR_OFF;
     // full(s): the stage's A tile (one arrival per producer warp) and B tile (the TMA
     // thread's expect_tx arrival and the copies' bytes) are in place; with CTA pairs
-    // the odd CTA's barrier counts its A tile only (its B half lands on the even CTA's)
+    // the even CTA's barrier counts both CTAs' producer warps and B halves (the odd
+    // CTA's barrier is unused)
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
     auto acc_full = [&](int b) { return bar0 + 8u * (3 * NS + b); };
     auto acc_empty = [&](int b) { return bar0 + 8u * (3 * NS + 2 + b); };
     const uint32_t drain = bar0 + 8u * (3 * NS + 4);
-    // CG = 2, even CTA: the odd CTA's A tiles of stages s .. s + RG - 1 are in place
-    auto peer_ready = [&](int s) { return bar0 + 8u * (3 * NS + 5 + s); };
     // AM: A stage sa is in TMEM (every producer warp of both CTAs has arrived;
     // on the even CTA) / free again (the MMAs reading it completed; both CTAs)
     auto afull = [&](int sa) { return bar0 + 8u * (NS + sa); };
-    auto aempty = [&](int sa) { return peer_ready(sa); };
+    auto aempty = [&](int sa) { return bar0 + 8u * (3 * NS + 5 + sa); };
     static_assert(8 * (4 * NS + 5) + 4 <= MX_CONST_OFF - MX_BAR_OFF, "barrier block");
     uint32_t *tmem_holder = (uint32_t *)(smem + MX_BAR_OFF + 8 * (4 * NS + 5));
 
@@ -571,10 +532,12 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(full(s), AM ? 1 : MX_APROD + (leader ? 1 : 0));
+            mbar_init(full(s), AM || !leader ? 1 : CG * MX_APROD + 1);
             mbar_init(empty(s), 1);  // the MMA commit (CG = 2: the pair's commit reaches both CTAs)
-            mbar_init(peer_ready(s), 1);  // AM: aempty
-            if (AM && s < NSA) mbar_init(afull(s), 2 * MX_APROD);
+            if (AM && s < NSA) {
+                mbar_init(afull(s), 2 * MX_APROD);
+                mbar_init(aempty(s), 1);
+            }
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
@@ -667,39 +630,8 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
             }
         }
     } else if (warp == 5 && !leader) {
-        // ---------------- CG = 2, odd CTA: tells the even CTA when its A tiles are in ----------------
-        // (its B halves are counted on the even CTA's barriers by the copies themselves;
-        // with A in TMEM the producers arrive on the even CTA's barriers directly)
-        if (!AM && lane == 0) {
-            const uint32_t rank0 = crank - 1u;
-            int stage = 0;
-            uint32_t phase = 0;
-            bool ok = true;
-            int pending = -1;  // first stage of a group not reported yet
-            for (int it = cid; it < n_work && ok; it += ncl) {
-                const ItemInfo I = item_info<DT, KS>(P, P.items[it], CL, sub);
-                if (I.skip) continue;
-                for (int c = 0; c < I.C && ok; ++c) {
-                    for (int kc = 0; kc < I.KC; ++kc) {
-                        if (!mbar_wait(full(stage), phase, P.timeout, lim)) {
-                            ok = false;
-                            break;
-                        }
-                        if (stage % RG == 0) pending = stage;
-                        if (stage % RG == RG - 1) {
-                            mbar_arrive_remote(mapa_rank(peer_ready(pending), rank0));
-                            pending = -1;
-                        }
-                        if (++stage == NS) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
-                    }
-                }
-            }
-            // the last group may be short: its stages are all in
-            if (ok && pending >= 0) mbar_arrive_remote(mapa_rank(peer_ready(pending), rank0));
-        }
+        // CG = 2, odd CTA: no MMA issuer (its producers and copies report to the even
+        // CTA's barriers directly)
     } else if (warp == 5 && AM) {
         // ---------------- MMA issuer, A in TMEM ----------------
         if (lane == 0) {
@@ -792,8 +724,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)abuf * MX_NACC;
                     for (int kc = 0; kc < I.KC; ++kc) {
-                        if (!mbar_wait(full(stage), phase, P.timeout, lim) ||
-                            (CG == 2 && stage % RG == 0 && !mbar_wait_cluster(peer_ready(stage), phase, P.timeout, lim))) {
+                        if (!mbar_wait(full(stage), phase, P.timeout, lim)) {
                             ok = false;
                             break;
                         }
@@ -932,7 +863,13 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                     // the MMA thread's wait for that stage runs out
                     const bool hold = P.withhold && !withheld && blockIdx.x == 0 && pi == 0;
                     withheld |= hold;
-                    if (lane == 0 && !hold) mbar_arrive(full(stage));
+                    // the odd CTA's warps arrive on the even CTA's barrier without a release:
+                    // their stores are visible to the async proxy (the fence above), and the
+                    // tensor core reading them is this SM's own
+                    if (lane == 0 && !hold) {
+                        if (leader) mbar_arrive(full(stage));
+                        else mbar_arrive_remote_relaxed(mapa_rank(full(stage), crank - 1u));
+                    }
                     if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
@@ -1092,7 +1029,8 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                 __syncwarp();
                 if (lane == 0) {
                     if (leader) mbar_arrive(acc_empty(abuf));
-                    else mbar_arrive_remote(mapa_rank(acc_empty(abuf), crank - 1u));  // the even CTA reuses it
+                    // the even CTA reuses it (its loads are complete: no release needed)
+                    else mbar_arrive_remote_relaxed(mapa_rank(acc_empty(abuf), crank - 1u));
                 }
                 abuf ^= 1;
                 if (abuf == 0) aphase ^= 1u;
