@@ -985,7 +985,7 @@ __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p
                                 const PairState *__restrict__ st, const unsigned int *__restrict__ colmax,
                                 const i128 *__restrict__ tpart, const float *__restrict__ cpart,
                                 const float *__restrict__ cpart1, i128 *__restrict__ t_ex, i128 *__restrict__ s1o,
-                                ColConst *__restrict__ cc)
+                                ColConst *__restrict__ cc, float *__restrict__ ct)
 {
     const int d = o.d;
     const int64_t idx = (int64_t)p0 * o.d_pad + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -995,6 +995,7 @@ __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p
     ColConst c{0.0f, 0.0f, 0.0f, 0.0f};
     if (j >= d || st[p].status != ST_OK) {
         cc[idx] = c;
+        ct[idx] = 0.0f;
         if (j < d) {
             t_ex[(int64_t)p * d + j] = 0;
             s1o[(int64_t)p * d + j] = 0;
@@ -1026,6 +1027,7 @@ __global__ void k_zstats_reduce(const PairMeta *__restrict__ meta, int p0, int p
         c.c = __fmul_ru(gam, csum);
     }
     cc[idx] = c;
+    ct[idx] = c.t;
 }
 
 // ---------------------------------------------------------------------------
@@ -1127,7 +1129,7 @@ void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax,
                    const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,
-                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, bool tok_layout, cudaStream_t st)
+                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, float *ct, bool tok_layout, cudaStream_t st)
 {
     if (sp.c1 <= sp.c0 || sp.p1 <= sp.p0) return;
     const unsigned nc = (unsigned)(sp.c1 - sp.c0);
@@ -1141,7 +1143,7 @@ void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan 
         k_zstats_partial<DT_BF16><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, colL1, tpart, cpart,
                                                       cpart1, zq, zq_ld);
     k_zstats_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * o.d_pad, 256), 256, 0, st>>>(
-        meta, sp.p0, sp.p1, o, pst, colmax, tpart, cpart, cpart1, t_ex, s1o, cc);
+        meta, sp.p0, sp.p1, o, pst, colmax, tpart, cpart, cpart1, t_ex, s1o, cc, ct);
 }
 
 void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,

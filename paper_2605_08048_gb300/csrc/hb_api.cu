@@ -509,6 +509,7 @@ struct Bufs {
     float *cpart, *cpart1;
     i128 *t_ex, *s1o;
     ColConst *cc;
+    float *ct;
     unsigned short *zq;
     uint32_t *bits;
     RecheckItem *list;
@@ -550,6 +551,7 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
         b.t_ex = cv.take<i128>((size_t)P * d);
         b.s1o = cv.take<i128>((size_t)P * d);
         b.cc = cv.take<ColConst>((size_t)P * pl.o.d_pad);
+        b.ct = cv.take<float>((size_t)P * pl.o.d_pad);
         b.zq = pl.o.path == HB_PATH_MIXED
                    ? cv.take<unsigned short>((size_t)pl.o.slices * pl.o.d_pad * pl.total_rows_pad)
                    : nullptr;
@@ -729,7 +731,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         // step 4: Z statistics, fixed-point slices, T_obs
         if (pieces == 1) xmark(ex, 1);
         launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.colL1, b.part, b.cpart, b.cpart1, b.zq, zq_ld,
-                      b.t_ex, b.s1o, b.cc, tok_layout, s);
+                      b.t_ex, b.s1o, b.cc, b.ct, tok_layout, s);
         launch_tobs(b.meta, sp, o, b.t_ex, b.s1o, b.cc, b.st, s);
         CK(cudaGetLastError());
     }
@@ -753,6 +755,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
             ma.o = o;
             ma.st = b.st;
             ma.cc = b.cc;
+            ma.ct = b.ct;
             ma.bits = b.bits;
             ma.zq = b.zq;
             ma.zq_ld = zq_ld;

@@ -90,6 +90,7 @@ struct MixedParams {
     RunOpts o;
     PairState *st;
     const ColConst *cc;
+    const float *ct;                 // column totals t, [pair][d_pad], zero past d
     const uint32_t *bits;
     const WorkItem *items;
     int n_work;                      // items, or -1: read *n_work_dev
@@ -227,10 +228,14 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// 4-byte asynchronous copy global -> shared (cp.async), and its groups
+// 4- and 16-byte asynchronous copies global -> shared (cp.async), and their groups
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
@@ -886,15 +891,15 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
         float *const cbase = (float *)(smem + MX_CONST_OFF) + warp * 4 * MX_NACC;
         auto fetch = [&](int p, int c, int cw, int buf) {
             float *t = cbase + buf * 2 * MX_NACC;
-            for (int jj = lane; jj < cw; jj += 32) {
-                const int j = c * cw + jj;
-                if (j < o.d) {
-                    const ColConst *q = P.cc + (int64_t)p * o.d_pad + j;
-                    cp_async4(t + jj, &q->t);
-                    if (DT == DT_F32) cp_async4(t + MX_NACC + jj, &q->q_hi);
-                } else {
-                    t[jj] = 0.f;  // columns past d
-                    t[MX_NACC + jj] = 0.f;
+            // totals: 16-byte copies of the contiguous array, which is zero past d (a
+            // tile never reaches past d_pad); FP32 storage also the slice scales
+            const float *src = P.ct + (int64_t)p * o.d_pad + c * cw;
+            for (int k = lane; k < cw / 4; k += 32) cp_async16(t + 4 * k, src + 4 * k);
+            if (DT == DT_F32) {
+                for (int jj = lane; jj < cw; jj += 32) {
+                    const int j = c * cw + jj;
+                    if (j < o.d) cp_async4(t + MX_NACC + jj, &P.cc[(int64_t)p * o.d_pad + j].q_hi);
+                    else t[MX_NACC + jj] = 0.f;
                 }
             }
             cp_async_commit();
@@ -1194,6 +1199,7 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     prm.o = a.o;
     prm.st = a.st;
     prm.cc = a.cc;
+    prm.ct = a.ct;
     prm.bits = a.bits;
     prm.items = a.items;
     prm.n_work = a.n_work;
