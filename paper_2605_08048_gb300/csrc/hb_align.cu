@@ -668,9 +668,18 @@ __device__ __forceinline__ void fixed_split(float z, float qh, int S, float &hi,
     }
 }
 
-// The slice matrix holds slice s of column j in row s * d_pad + j, tokens
-// contiguous (all pairs' tokens side by side, each pair from its z_row).
+// The slice matrix holds slice s of column j in row s * d_pad + j, over the
+// token positions of all pairs side by side (each pair from its z_row), in
+// blocks of 64 tokens: block k holds every row's tokens 64k .. 64k + 63
+// (128 bytes a row), so that one TMA box (64 tokens x up to 128 rows) is one
+// contiguous piece and a pair's slices one contiguous range, whatever the
+// batch size (rows of all pairs' tokens would put every row of a box on its
+// own memory page).
 __device__ __forceinline__ int64_t slice_row(int j, int s, int d_pad) { return (int64_t)s * d_pad + j; }
+__device__ __forceinline__ int64_t zq_index(int64_t t, int64_t row, int64_t zq_rows)
+{
+    return ((t >> 6) * zq_rows + row) * 64 + (t & 63);
+}
 
 // One block (256 threads) per row chunk, tiles of ZS_T columns.  Phase A:
 // thread (column, 16-row part) reads its values (coalesced across columns),
@@ -691,7 +700,7 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
                                                         const unsigned long long *__restrict__ colL1,
                                                         i128 *__restrict__ tpart, float *__restrict__ cpart,
                                                         float *__restrict__ cpart1,
-                                                        unsigned short *__restrict__ zq, int64_t zq_ld)
+                                                        unsigned short *__restrict__ zq)
 {
     __shared__ unsigned short sq[3][ZS_T][CHUNK_ROWS + 2];
     __shared__ i128 acc_s[ZS_PARTS][ZS_T];
@@ -759,9 +768,9 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
             const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
             for (int c = wp; c < ZS_T && j0 + c < d; c += (int)(blockDim.x >> 5)) {
                 for (int s = 0; s < S; ++s) {
-                    unsigned short *dst = zq + slice_row(j0 + c, s, o.d_pad) * zq_ld + pm.z_row;
-                    for (int r = ln; r < ch.nrows; r += 32) dst[tok0 + r] = sq[s][c][r];
-                    for (int k = ln; k < npad; k += 32) dst[pm.N + k] = 0;
+                    const int64_t row = slice_row(j0 + c, s, o.d_pad), zr = (int64_t)S * o.d_pad;
+                    for (int r = ln; r < ch.nrows; r += 32) zq[zq_index(pm.z_row + tok0 + r, row, zr)] = sq[s][c][r];
+                    for (int k = ln; k < npad; k += 32) zq[zq_index(pm.z_row + pm.N + k, row, zr)] = 0;
                 }
             }
         }
@@ -854,7 +863,7 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
                                                     const unsigned long long *__restrict__ colL1,
                                                     i128 *__restrict__ tpart, float *__restrict__ cpart,
                                                     float *__restrict__ cpart1,
-                                                    unsigned short *__restrict__ zq, int64_t zq_ld)
+                                                    unsigned short *__restrict__ zq)
 {
     const int ci = c0 + (int)blockIdx.x;  // chunk index
     const RowChunk ch = chunks[ci];
@@ -878,14 +887,15 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
     // row rb of the chunk (the lane's first position) in 16-byte units; only rows
     // with ok[i] are read
     const int64_t zr = (pm.z_row + tok0 + rb) * d16;
-    const int64_t lo_off = (int64_t)d_pad * zq_ld;  // second slice: d_pad rows further
+    const int64_t zrows = 2 * (int64_t)d_pad;      // rows of the slice matrix (two BF16 grid slices)
+    const int64_t lo_off = (int64_t)d_pad * 64;     // second slice: d_pad rows further in the token block
 
     for (int c8 = wp; c8 < d16; c8 += 8) {
         const int j = 8 * c8;
         uint4 v[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] = ok[i] ? __ldg(Z + zr + i * d16 + c8) : make_uint4(0u, 0u, 0u, 0u);
-        unsigned short *dh = zq + (int64_t)j * zq_ld + tq;
+        unsigned short *dh = zq + zq_index(tq, j, zrows);  // the lane's 4 positions lie in one 64-token block
         // lane e < 8 keeps column j + e's reductions
         int my_ik = 0, my_ik2 = 0, my_eg = 0, my_eg2 = 0;
         bool my_split = false;
@@ -939,7 +949,7 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
                         dl[i] = (unsigned short)((i & 1) ? lp >> 16 : lp);
                     }
             }
-            dh += zq_ld;
+            dh += 64;  // the next row of the block
             const int ik = __reduce_add_sync(0xffffffffu, sk);
             const int ik2 = __reduce_add_sync(0xffffffffu, sk2);
             const float c1 = __any_sync(0xffffffffu, ra1 != 0.0f) ? warp_sum_ru(ra1) : 0.0f;
@@ -974,7 +984,7 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
         // the last chunk of the pair also zero-fills the padded tokens of the slices
         for (int k = ln; k < 16 * npad; k += 32) {
             const int e = k / (2 * npad), s = (k / npad) & 1, t = k % npad;
-            zq[slice_row(j + e, s, d_pad) * zq_ld + pm.z_row + pm.N + t] = 0;
+            zq[zq_index(pm.z_row + pm.N + t, slice_row(j + e, s, d_pad), zrows)] = 0;
         }
     }
 }
@@ -1129,19 +1139,19 @@ void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax,
                    const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,
-                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, float *ct, bool tok_layout, cudaStream_t st)
+                   i128 *t_ex, i128 *s1o, ColConst *cc, float *ct, bool tok_layout, cudaStream_t st)
 {
     if (sp.c1 <= sp.c0 || sp.p1 <= sp.p0) return;
     const unsigned nc = (unsigned)(sp.c1 - sp.c0);
     if (o.dtype == DT_F32)
         k_zstats_partial<DT_F32><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, colL1, tpart, cpart,
-                                                     cpart1, zq, zq_ld);
+                                                     cpart1, zq);
     else if (tok_layout)
         k_zstats_tok<<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, static_cast<const uint4 *>(Z), colL1, tpart,
-                                         cpart, cpart1, zq, zq_ld);
+                                         cpart, cpart1, zq);
     else
         k_zstats_partial<DT_BF16><<<nc, 256, 0, st>>>(meta, chunks, sp.c0, o, pst, Z, colmax, colL1, tpart, cpart,
-                                                      cpart1, zq, zq_ld);
+                                                      cpart1, zq);
     k_zstats_reduce<<<cdiv_((int64_t)(sp.p1 - sp.p0) * o.d_pad, 256), 256, 0, st>>>(
         meta, sp.p0, sp.p1, o, pst, colmax, tpart, cpart, cpart1, t_ex, s1o, cc, ct);
 }

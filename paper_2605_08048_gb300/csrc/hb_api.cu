@@ -730,7 +730,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
         CK(cudaGetLastError());
         // step 4: Z statistics, fixed-point slices, T_obs
         if (pieces == 1) xmark(ex, 1);
-        launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.colL1, b.part, b.cpart, b.cpart1, b.zq, zq_ld,
+        launch_zstats(b.meta, b.chunks, sp, o, b.st, Z, b.colmax, b.colL1, b.part, b.cpart, b.cpart1, b.zq,
                       b.t_ex, b.s1o, b.cc, b.ct, tok_layout, s);
         launch_tobs(b.meta, sp, o, b.t_ex, b.s1o, b.cc, b.st, s);
         CK(cudaGetLastError());

@@ -29,7 +29,7 @@ void launch_reflect(const PairMeta *meta, const RowChunk *chunks, const PairSpan
 void launch_zstats(const PairMeta *meta, const RowChunk *chunks, const PairSpan &sp, const RunOpts &o,
                    const PairState *pst, const void *Z, const unsigned int *colmax,
                    const unsigned long long *colL1, i128 *tpart, float *cpart, float *cpart1, unsigned short *zq,
-                   int64_t zq_ld, i128 *t_ex, i128 *s1o, ColConst *cc, float *ct, bool tok_layout, cudaStream_t st);
+                   i128 *t_ex, i128 *s1o, ColConst *cc, float *ct, bool tok_layout, cudaStream_t st);
 void launch_tobs(const PairMeta *meta, const PairSpan &sp, const RunOpts &o, const i128 *t_ex, const i128 *s1o,
                  const ColConst *cc, PairState *pst, cudaStream_t st);
 void launch_labels_rows(uint64_t seed, uint32_t stream, int n, int N, int64_t b0, int64_t count, uint32_t *out,
@@ -63,7 +63,7 @@ struct MixedArgs {
     const float *ct;  // column totals t alone, [pair][d_pad] (zero past d)
     const uint32_t *bits;
     const unsigned short *zq;
-    int64_t zq_ld;    // tokens per slice row
+    int64_t zq_ld;    // token positions of the slice matrix (a multiple of 64)
     int64_t zq_rows;  // slice rows
     const WorkItem *items;
     int n_work;                      // >= 0: items; < 0: the count is *n_work_dev (written on the device)

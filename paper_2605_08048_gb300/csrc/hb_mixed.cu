@@ -184,23 +184,26 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+// The slice matrix as a 3-D tensor: 64 tokens (128 bytes, the innermost
+// coordinate, always 0 here), rows, 64-token blocks.  A box is 64 tokens x
+// box_rows rows of one block.
+__device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap *map, int y, int kb, uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
             dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        "l"((uint64_t)map), "r"(0), "r"(y), "r"(kb), "r"(bar)
         : "memory");
 }
 
 // CTA pairs: a tile into this CTA's shared memory whose completion is counted
 // on an mbarrier of the pair's even CTA (bar: shared::cluster address)
-__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+__device__ __forceinline__ void tma_load_rows_pair(uint32_t dst, const CUtensorMap *map, int y, int kb, uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(0), "r"(y), "r"(kb), "r"(bar)
         : "memory");
 }
 
@@ -606,10 +609,11 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
 #pragma unroll
                             for (int k = 0; k < 8; ++k) {
                                 if (k >= nb) break;
-                                if (CG == 1) tma_load_2d(adst + (uint32_t)(k * br) * 128u, &tmap, x0 + a * MX_K,
-                                                         yb[k] + c * I.cw, bar);
-                                else tma_load_2d_pair(adst + (uint32_t)(k * br) * 128u, &tmap, x0 + a * MX_K,
-                                                      yb[k] + c * I.cw, bar);
+                                // (a pair's tokens start at a multiple of 64: block x0 / 64 + a)
+                                if (CG == 1) tma_load_rows(adst + (uint32_t)(k * br) * 128u, &tmap, yb[k] + c * I.cw,
+                                                           (x0 >> 6) + a, bar);
+                                else tma_load_rows_pair(adst + (uint32_t)(k * br) * 128u, &tmap, yb[k] + c * I.cw,
+                                                        (x0 >> 6) + a, bar);
                             }
                         }
                         ++issued;
@@ -1183,11 +1187,12 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode(err);
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t gdim[2] = {(cuuint64_t)a.zq_ld, (cuuint64_t)a.zq_rows};
-    const cuuint64_t gstride[1] = {(cuuint64_t)a.zq_ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)MX_K, (cuuint32_t)br};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.zq, gdim, gstride, box, estr,
+    // the slice matrix in 64-token blocks: (64 tokens, zq_rows rows, zq_ld / 64 blocks)
+    const cuuint64_t gdim[3] = {(cuuint64_t)MX_K, (cuuint64_t)a.zq_rows, (cuuint64_t)(a.zq_ld / MX_K)};
+    const cuuint64_t gstride[2] = {(cuuint64_t)MX_K * 2, (cuuint64_t)a.zq_rows * MX_K * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)MX_K, (cuuint32_t)br, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)a.zq, gdim, gstride, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
