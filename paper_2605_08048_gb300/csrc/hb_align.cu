@@ -680,6 +680,14 @@ __device__ __forceinline__ int64_t zq_index(int64_t t, int64_t row, int64_t zq_r
 {
     return ((t >> 6) * zq_rows + row) * 64 + (t & 63);
 }
+// BF16 grid slices also interleave the two halves of every 32-token group of
+// a pair: pair token t sits at position slice_pos(t) = 32 (t / 32) +
+// 2 (t % 16) + (t / 16) % 2, i.e. the order 0, 16, 1, 17, ..., 15, 31.  The
+// GEMM sums over positions, so any order serves; this one puts tokens j and
+// j + 16 into one 32-bit word of the K dimension, which are bits j and j + 16
+// of a label word: two operations expand a word, with no bit shuffle.  FP32
+// fixed-point slices keep the token order.
+__device__ __forceinline__ int64_t slice_pos(int64_t t) { return (t & ~(int64_t)31) | ((t & 15) << 1) | ((t >> 4) & 1); }
 
 // One block (256 threads) per row chunk, tiles of ZS_T columns.  Phase A:
 // thread (column, 16-row part) reads its values (coalesced across columns),
@@ -769,8 +777,14 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
             for (int c = wp; c < ZS_T && j0 + c < d; c += (int)(blockDim.x >> 5)) {
                 for (int s = 0; s < S; ++s) {
                     const int64_t row = slice_row(j0 + c, s, o.d_pad), zr = (int64_t)S * o.d_pad;
-                    for (int r = ln; r < ch.nrows; r += 32) zq[zq_index(pm.z_row + tok0 + r, row, zr)] = sq[s][c][r];
-                    for (int k = ln; k < npad; k += 32) zq[zq_index(pm.z_row + pm.N + k, row, zr)] = 0;
+                    if (DT == DT_BF16) {
+                        for (int r = ln; r < ch.nrows; r += 32)
+                            zq[zq_index(pm.z_row + slice_pos(tok0 + r), row, zr)] = sq[s][c][r];
+                        for (int k = ln; k < npad; k += 32) zq[zq_index(pm.z_row + slice_pos(pm.N + k), row, zr)] = 0;
+                    } else {
+                        for (int r = ln; r < ch.nrows; r += 32) zq[zq_index(pm.z_row + tok0 + r, row, zr)] = sq[s][c][r];
+                        for (int k = ln; k < npad; k += 32) zq[zq_index(pm.z_row + pm.N + k, row, zr)] = 0;
+                    }
                 }
             }
         }
@@ -792,10 +806,12 @@ __global__ void __launch_bounds__(256) k_zstats_partial(const PairMeta *__restri
 
 // The same outputs for the tensor-core path on BF16 storage with d a
 // multiple of 8, with lanes along tokens.  Warp w takes the 8-column groups
-// w, w + 8, ... ; lane l takes the four consecutive token positions
-// 4l .. 4l + 3 of the chunk, position q being token tok0 - g + q with
-// g = tok0 mod 4, so that a lane's four values of one slice column leave in
-// one aligned 8-byte store (the host keeps g + nrows <= 128).  The column
+// w, w + 8, ... ; the chunk lies in a window of four 32-token groups that
+// starts g = tok0 mod 32 tokens before it (the host keeps g + nrows <= 128),
+// and lane l takes the window's tokens 32 (l / 8) + {2k, 2k + 1, 2k + 16,
+// 2k + 17}, k = l % 8, whose slice positions 32 (l / 8) + 4k .. + 3 are
+// contiguous (slice_pos), so that a lane's four values of one slice column
+// leave in one aligned 8-byte store.  The column
 // total is k_sum g + k2_sum g2 (integer warp sums of the slice multiples)
 // plus the rare nonzero second residuals added exactly out of line (columns
 // outside the split range add every value exactly, with the oracle's rule
@@ -871,22 +887,24 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
     if (st[ch.pair].status != ST_OK) return;
     const int d = o.d, d_pad = o.d_pad;
     const int64_t tok0 = (ch.side ? pm.n : 0) + ch.row0;  // token index within the pair
-    const int g = (int)(tok0 & 3);
+    const int g = (int)(tok0 & 31);
     const bool last = ch.side == 1 && ch.row0 + ch.nrows == pm.m;
     const int npad = last ? pm.N_pad - pm.N : 0;
     const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    const int rb = 4 * ln - g;  // chunk row of the lane's first position
+    // chunk rows of the lane's four tokens 2k, 2k + 1, 2k + 16, 2k + 17 of its group
+    const int wb = 32 * (ln >> 3) + 2 * (ln & 7) - g;
+    const int rbi[4] = {wb, wb + 1, wb + 16, wb + 17};
     bool ok[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) ok[i] = rb + i >= 0 && rb + i < ch.nrows;
+    for (int i = 0; i < 4; ++i) ok[i] = rbi[i] >= 0 && rbi[i] < ch.nrows;
     const bool full = ok[0] && ok[1] && ok[2] && ok[3];
     const unsigned int okm = (ok[0] ? 1u : 0u) | (ok[1] ? 2u : 0u) | (ok[2] ? 4u : 0u) | (ok[3] ? 8u : 0u);
-    const int64_t tq = pm.z_row + tok0 - g + 4 * ln;  // slice-row offset of the lane's first position
+    // position of the lane's first value (token 2k; then 2k + 16, 2k + 1, 2k + 17)
+    const int64_t tq = pm.z_row + tok0 - g + 32 * (ln >> 3) + 4 * (ln & 7);
     const unsigned long long *cl = colL1 + (int64_t)ch.pair * d_pad;
     const int d16 = d / 8;  // 16-byte units per row
-    // row rb of the chunk (the lane's first position) in 16-byte units; only rows
-    // with ok[i] are read
-    const int64_t zr = (pm.z_row + tok0 + rb) * d16;
+    // row of the chunk's first token in 16-byte units; only rows with ok[i] are read
+    const int64_t zr = (pm.z_row + tok0) * d16;
     const int64_t zrows = 2 * (int64_t)d_pad;      // rows of the slice matrix (two BF16 grid slices)
     const int64_t lo_off = (int64_t)d_pad * 64;     // second slice: d_pad rows further in the token block
 
@@ -894,7 +912,7 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
         const int j = 8 * c8;
         uint4 v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = ok[i] ? __ldg(Z + zr + i * d16 + c8) : make_uint4(0u, 0u, 0u, 0u);
+        for (int i = 0; i < 4; ++i) v[i] = ok[i] ? __ldg(Z + zr + (int64_t)rbi[i] * d16 + c8) : make_uint4(0u, 0u, 0u, 0u);
         unsigned short *dh = zq + zq_index(tq, j, zrows);  // the lane's 4 positions lie in one 64-token block
         // lane e < 8 keeps column j + e's reductions
         int my_ik = 0, my_ik2 = 0, my_eg = 0, my_eg2 = 0;
@@ -931,22 +949,23 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
             }
             const int sk = __float2int_rz(fk), sk2 = __float2int_rz(fk2);
             // the slice values have at most 8 significant bits: the high halves of
-            // their FP32 bits are their BF16 bits
-            const uint32_t hp0 = __byte_perm(__float_as_uint(kf[0]), __float_as_uint(kf[1]), 0x7632);
-            const uint32_t hp1 = __byte_perm(__float_as_uint(kf[2]), __float_as_uint(kf[3]), 0x7632);
-            const uint32_t lp0 = __byte_perm(__float_as_uint(k2f[0]), __float_as_uint(k2f[1]), 0x7632);
-            const uint32_t lp1 = __byte_perm(__float_as_uint(k2f[2]), __float_as_uint(k2f[3]), 0x7632);
+            // their FP32 bits are their BF16 bits; positions in the order of tokens
+            // 2k, 2k + 16, 2k + 1, 2k + 17 (values 0, 2, 1, 3)
+            const uint32_t hp0 = __byte_perm(__float_as_uint(kf[0]), __float_as_uint(kf[2]), 0x7632);
+            const uint32_t hp1 = __byte_perm(__float_as_uint(kf[1]), __float_as_uint(kf[3]), 0x7632);
+            const uint32_t lp0 = __byte_perm(__float_as_uint(k2f[0]), __float_as_uint(k2f[2]), 0x7632);
+            const uint32_t lp1 = __byte_perm(__float_as_uint(k2f[1]), __float_as_uint(k2f[3]), 0x7632);
             unsigned short *dl = dh + lo_off;
             if (full) {
                 *reinterpret_cast<uint2 *>(dh) = make_uint2(hp0, hp1);
                 *reinterpret_cast<uint2 *>(dl) = make_uint2(lp0, lp1);
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (ok[i]) {
-                        const uint32_t hp = i < 2 ? hp0 : hp1, lp = i < 2 ? lp0 : lp1;
-                        dh[i] = (unsigned short)((i & 1) ? hp >> 16 : hp);
-                        dl[i] = (unsigned short)((i & 1) ? lp >> 16 : lp);
+                for (int q = 0; q < 4; ++q)
+                    if (ok[(q >> 1) | ((q & 1) << 1)]) {  // position q holds value 0, 2, 1, 3
+                        const uint32_t hp = q < 2 ? hp0 : hp1, lp = q < 2 ? lp0 : lp1;
+                        dh[q] = (unsigned short)((q & 1) ? hp >> 16 : hp);
+                        dl[q] = (unsigned short)((q & 1) ? lp >> 16 : lp);
                     }
             }
             dh += 64;  // the next row of the block
@@ -984,7 +1003,7 @@ __global__ void __launch_bounds__(256, 3) k_zstats_tok(const PairMeta *__restric
         // the last chunk of the pair also zero-fills the padded tokens of the slices
         for (int k = ln; k < 16 * npad; k += 32) {
             const int e = k / (2 * npad), s = (k / npad) & 1, t = k % npad;
-            zq[zq_index(pm.z_row + pm.N + t, slice_row(j + e, s, d_pad), zrows)] = 0;
+            zq[zq_index(pm.z_row + slice_pos(pm.N + t), slice_row(j + e, s, d_pad), zrows)] = 0;
         }
     }
 }

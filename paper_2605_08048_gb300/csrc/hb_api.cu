@@ -424,10 +424,10 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int64_t r = 0; r < np; r += CHUNK_ROWS)
             pl.chunks.push_back(RowChunk{(int)p, 0, (int)r, (int)std::min<int64_t>(CHUNK_ROWS, np - r)});
         pm.nchunk_x = (int)pl.chunks.size() - pm.chunk0;
-        // the first Y chunk ends where token n + rows is a multiple of 4: every
-        // chunk then starts at a token index t with (t mod 4) + rows <= 128
+        // the first Y chunk ends where token n + rows is a multiple of 32: every
+        // chunk then starts at a token index t with (t mod 32) + rows <= 128
         for (int64_t r = 0; r < mp;) {
-            const int64_t rows = std::min<int64_t>(r == 0 ? CHUNK_ROWS - (np & 3) : CHUNK_ROWS, mp - r);
+            const int64_t rows = std::min<int64_t>(r == 0 ? CHUNK_ROWS - (np & 31) : CHUNK_ROWS, mp - r);
             pl.chunks.push_back(RowChunk{(int)p, 1, (int)r, (int)rows});
             r += rows;
         }

@@ -432,13 +432,18 @@ __device__ __forceinline__ uint32_t unshuffle32(uint32_t x)
     return x;
 }
 
-// One label word (32 tokens) -> 16 words of two BF16 labels 0.0 / 1.0: word j
-// holds tokens 2j (low half) and 2j + 1 (high half).  After unshuffle32,
-// word j is bits j and 16 + j of x times 0x3F80 (BF16 1.0) in each half; as
-// 0x3F80 = 127 * 2^7, for j < 8 the shift folds into the multiplier.
+// One label word (32 tokens) -> 16 words of two BF16 labels 0.0 / 1.0, the
+// K positions 2j (low half) and 2j + 1 (high half) of the word's 32 slice
+// positions in word j.  BF16 grid slices hold tokens j and j + 16 there (the
+// slices interleave the halves of every 32-token group), i.e. bits j and
+// j + 16 of w; FP32 fixed-point slices hold tokens 2j and 2j + 1, which
+// unshuffle32 moves to bits j and j + 16.  Word j is then those two bits
+// times 0x3F80 (BF16 1.0) in each half; as 0x3F80 = 127 * 2^7, for j < 8 the
+// shift folds into the multiplier.
+template <int DT>
 __device__ __forceinline__ void expand_word(uint32_t w, uint32_t (&v)[16])
 {
-    const uint32_t x = unshuffle32(w), x8 = x >> 8;
+    const uint32_t x = DT == DT_BF16 ? w : unshuffle32(w), x8 = x >> 8;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         v[j] = (x & (0x00010001u << j)) * (0x3F80u >> j);
@@ -820,7 +825,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         break;
                     }
                     uint32_t v[16];
-                    expand_word(rw[0], v);
+                    expand_word<DT>(rw[0], v);
 #pragma unroll
                     for (int i = 0; i + 1 < MX_PF; ++i) rw[i] = rw[i + 1];
                     rw[MX_PF - 1] = word(knext);
@@ -858,7 +863,7 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
                         rw[MX_PF - 1] = word(knext);
                         if (++knext == QA) knext = 0;
                         uint32_t v[16];
-                        expand_word(wd, v);
+                        expand_word<DT>(wd, v);
 #pragma unroll
                         for (int cl = 0; cl < 4; ++cl) {
                             const int ch = 4 * half + cl;  // 16-byte chunk of the row: 8 tokens

@@ -53,7 +53,7 @@ def test_layout_invariants(case, path, dtype):
 
     # row chunks: pair-major, X rows then Y rows, each side covered in order by
     # chunks of at most CHUNK_ROWS rows; every chunk starts at a token index t
-    # with (t mod 4) + rows <= CHUNK_ROWS (one warp's 4 positions per lane)
+    # with (t mod 32) + rows <= CHUNK_ROWS (a warp covers four 32-token groups)
     first = np.zeros(P + 1, dtype=np.int64)
     k = 0
     for p in range(P):
@@ -64,7 +64,7 @@ def test_layout_invariants(case, path, dtype):
                 pair, sd, row0, nr = ch[k]
                 assert (pair, sd, row0) == (p, side, r0) and 1 <= nr <= CHUNK_ROWS
                 tok0 = (n[p] if side else 0) + row0
-                assert tok0 % 4 + nr <= CHUNK_ROWS
+                assert tok0 % 32 + nr <= CHUNK_ROWS
                 r0 += nr
                 k += 1
             assert r0 == rows
