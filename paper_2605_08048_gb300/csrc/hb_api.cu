@@ -56,6 +56,9 @@ extern "C" hb_status hb_ctx_stage_times(hb_ctx *c, float *ms_out, int32_t *n_lau
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int LABEL_CHUNKS = 4;  // label-draw chunks of a mixed-path call
+// device counters of a call: [0] recheck items, [1] overflow, [2] timeout,
+// [3 + c] work items of chunk c's gathered pass
+constexpr int N_COUNTERS = 3 + LABEL_CHUNKS;
 constexpr int ALIGN_PIECES = 8;  // pieces of the host-to-device input copy, aligned as they arrive
 }
 
@@ -72,7 +75,7 @@ struct hb_ctx {
     bool timing = false;
     bool last_timed = false;
     cudaEvent_t tev[7] = {};
-    cudaEvent_t gev[2 * (LABEL_CHUNKS + 1)] = {};  // around each GEMM launch (and the gathered pass)
+    cudaEvent_t gev[4 * LABEL_CHUNKS] = {};  // around each chunk's GEMM launch and its gathered pass
     float last_ms[7] = {};
     int last_launches = 0;
     // Streams of a call: the caller's stream forks into `main` (highest
@@ -280,6 +283,11 @@ struct Plan {
     int nlc = 0;
     int lc_pair[LABEL_CHUNKS + 1] = {};
     int lc_item[LABEL_CHUNKS + 1] = {};
+    // the gathered pass of chunk c: its work list starts at lc_gi[c] (room for every
+    // listed relabelling of the chunk's pairs), and it runs if the chunk has
+    // single-slice items
+    int lc_gi[LABEL_CHUNKS + 1] = {};
+    bool lc_single[LABEL_CHUNKS] = {};
 };
 
 // every pair's X and Y rows and the rows of Z start on 16-byte boundaries
@@ -481,14 +489,21 @@ static hb_status make_plan(Plan &pl, int64_t P, const int64_t *n, const int64_t 
         for (int c = 1; c <= LABEL_CHUNKS; ++c)
             if (cuts[c] > pl.lc_pair[pl.nlc]) pl.lc_pair[++pl.nlc] = cuts[c];
         // item boundaries: items follow `order`, so count the items of each chunk's pairs
-        int it = 0;
+        int it = 0, gi = 0;
         pl.lc_item[0] = 0;
+        pl.lc_gi[0] = 0;
         for (int c = 0; c < pl.nlc; ++c) {
+            pl.lc_single[c] = false;
             for (int k = pl.lc_pair[c]; k < pl.lc_pair[c + 1]; ++k) {
                 const int p = order[k];
-                if (pl.init_bad[p] == 0) it += pl.meta[p].B_pad / (128 * pl.cl);
+                if (pl.init_bad[p] == 0) {
+                    it += pl.meta[p].B_pad / (128 * pl.cl);
+                    if (pl.meta[p].N <= o.s1_max) pl.lc_single[c] = true;
+                }
+                gi += pl.meta[p].B_pad / 128 + 1;
             }
             pl.lc_item[c + 1] = it;
+            pl.lc_gi[c + 1] = gi;
         }
     }
     return HB_OK;
@@ -557,7 +572,7 @@ static size_t carve(Carve &cv, Bufs &b, const Plan &pl, bool align_only, bool ow
                    : nullptr;
         b.bits = cv.take<uint32_t>(pl.total_label_words);
         b.list = cv.take<RecheckItem>(cap);
-        b.counters = cv.take<unsigned int>(4);
+        b.counters = cv.take<unsigned int>(N_COUNTERS);
         b.scratch = cv.take<double>((size_t)rgrid * 2 * d);
         b.out = cv.take<PairOut>(P);
         b.items = pl.o.path == HB_PATH_MIXED ? cv.take<WorkItem>(pl.items.size()) : nullptr;
@@ -600,10 +615,12 @@ static float gemm_ms(const Plan &pl, const cudaEvent_t *gev)
 {
     float total = 0.f;
     const int nl = std::max(pl.nlc, 1);
-    for (int c = 0; c <= nl; ++c) {
-        if (c == nl && pl.n_single == 0) break;  // the gathered pass runs only after a single-slice pass
+    for (int k = 0; k < 2 * nl; ++k) {
+        // launch k / 2 of chunk k / 2: its single-slice (or full) GEMM, then its gathered pass,
+        // which runs only after a single-slice pass
+        if ((k & 1) && !(pl.nlc ? pl.lc_single[k / 2] : pl.n_single > 0)) continue;
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, gev[2 * c], gev[2 * c + 1]) == cudaSuccess) total += ms;
+        if (cudaEventElapsedTime(&ms, gev[2 * k], gev[2 * k + 1]) == cudaSuccess) total += ms;
         else cudaGetLastError();  // not recorded: leave no sticky error for the next call
     }
     return total;
@@ -647,7 +664,11 @@ static int launch_count(const Plan &pl, unsigned int cap, int rgrid, bool host_i
         gemm = 0;
         for (int c = 0; c < pl.nlc; ++c) gemm += pl.lc_item[c + 1] > pl.lc_item[c] ? 1 : 0;
     }
-    if (mixed && pl.n_single) gemm += 2;  // the gathered pass: its work list and its GEMM
+    if (mixed && pl.n_single) {
+        // each chunk's gathered pass: its work list and its GEMM
+        if (pl.nlc == 0) gemm += 2;
+        for (int c = 0; c < pl.nlc; ++c) gemm += pl.lc_single[c] ? 2 : 0;
+    }
     return 7 * pieces + 1 + labels + gemm + 2 * (int)((cap + rgrid - 1) / rgrid);
 }
 
@@ -690,7 +711,7 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
     }
     CK(cudaMemsetAsync(b.colmax, 0, sizeof(unsigned int) * P * o.d_pad, s));
     if (b.colL1) CK(cudaMemsetAsync(b.colL1, 0, sizeof(unsigned long long) * P * o.d_pad, s));
-    CK(cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(b.counters, 0, N_COUNTERS * sizeof(unsigned int), s));
     if (mixed && o.d_pad != d)
         CK(cudaMemsetAsync(b.zq, 0, sizeof(unsigned short) * (size_t)o.slices * o.d_pad * pl.total_rows_pad, s));
 
@@ -777,28 +798,30 @@ static hb_status enqueue_test(const Exec &ex, const Plan &pl, const Bufs &b, voi
                 ma.items = b.items + (pl.nlc ? pl.lc_item[c] : 0);
                 ma.n_work = pl.nlc ? pl.lc_item[c + 1] - pl.lc_item[c] : (int)pl.items.size();
                 std::string err;
-                if (ex.gev) xrec(ex, ex.gev[2 * c]);
-                const cudaError_t e = launch_mixed(ma, s, err);
-                if (ex.gev) xrec(ex, ex.gev[2 * c + 1]);
+                if (ex.gev) xrec(ex, ex.gev[4 * c]);
+                cudaError_t e = launch_mixed(ma, s, err);
+                if (ex.gev) xrec(ex, ex.gev[4 * c + 1]);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
                     return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
                                 "mixed path launch failed: %s (%s)", cudaGetErrorString(e), err.c_str());
                 }
-            }
-            if (pl.n_single) {
-                // the gathered pass: every slice for the relabellings the single-slice pass
-                // left inside its band, in single CTAs (128 listed relabellings per item)
-                launch_gather_items(b.st, P, b.gitems, b.counters + 3, s);
-                ma.o.cg = 1;
-                ma.withhold = 0;
-                ma.items = b.gitems;
-                ma.n_work = -1;
-                ma.n_work_dev = b.counters + 3;
-                std::string err;
-                if (ex.gev) xrec(ex, ex.gev[2 * nl]);
-                const cudaError_t e = launch_mixed(ma, s, err);
-                if (ex.gev) xrec(ex, ex.gev[2 * nl + 1]);
+                if (!(pl.nlc ? pl.lc_single[c] : pl.n_single > 0)) continue;
+                // the chunk's gathered pass: every slice for the relabellings its single-slice
+                // pass left inside its band, in single CTAs (128 listed relabellings per
+                // item); it runs while the next chunk's labels are still being drawn
+                const int q0 = pl.nlc ? pl.lc_pair[c] : 0, q1 = pl.nlc ? pl.lc_pair[c + 1] : P;
+                WorkItem *gi = b.gitems + (pl.nlc ? pl.lc_gi[c] : 0);
+                launch_gather_items(b.st, pl.nlc ? b.order : nullptr, q0, q1, gi, b.counters + 3 + c, s);
+                MixedArgs mg = ma;
+                mg.o.cg = 1;
+                mg.withhold = 0;
+                mg.items = gi;
+                mg.n_work = -1;
+                mg.n_work_dev = b.counters + 3 + c;
+                if (ex.gev) xrec(ex, ex.gev[4 * c + 2]);
+                e = launch_mixed(mg, s, err);
+                if (ex.gev) xrec(ex, ex.gev[4 * c + 3]);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
                     return fail(e == cudaErrorNotSupported ? HB_ERR_UNSUPPORTED : HB_ERR_CUDA,
@@ -1185,7 +1208,7 @@ struct hb_plan {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t lab_ev[LABEL_CHUNKS] = {};
     cudaEvent_t tev[7] = {};
-    cudaEvent_t gev[2 * (LABEL_CHUNKS + 1)] = {};
+    cudaEvent_t gev[4 * LABEL_CHUNKS] = {};
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

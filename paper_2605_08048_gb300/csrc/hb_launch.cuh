@@ -80,7 +80,9 @@ struct MixedArgs {
     int sms;
 };
 // the gathered pass's work list: ceil(n_gather / 128) items per pair, *n_items of them
-void launch_gather_items(const PairState *st, int P, WorkItem *items, unsigned int *n_items, cudaStream_t s);
+// work items of the gathered pass for pairs order[p0 .. p1) (order null: p0 .. p1)
+void launch_gather_items(const PairState *st, const int *order, int p0, int p1, WorkItem *items,
+                         unsigned int *n_items, cudaStream_t s);
 cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err);
 
 // learned triage (hb_triage.cu)

@@ -1103,18 +1103,20 @@ __global__ void __launch_bounds__(MX_BOUND_THREADS, 1) k_mixed(const __grid_cons
 // ---------------------------------------------------------------------------
 // the gathered pass: one work item per 128 listed relabellings of a pair
 // ---------------------------------------------------------------------------
-// Single block: per pair the listed count n_gather, items in pair order.
-__global__ void k_gather_items(const PairState *__restrict__ st, int P, WorkItem *__restrict__ items,
-                               unsigned int *__restrict__ n_items)
+// Single block: per pair of order[q0 .. q1) (order null: pairs q0 .. q1) the
+// listed count n_gather, items in that order.
+__global__ void k_gather_items(const PairState *__restrict__ st, const int *__restrict__ order, int q0, int q1,
+                               WorkItem *__restrict__ items, unsigned int *__restrict__ n_items)
 {
     __shared__ unsigned int warp_tot[32];
     __shared__ unsigned int base_s;
     if (threadIdx.x == 0) base_s = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
-    for (int p0 = 0; p0 < P; p0 += (int)blockDim.x) {
-        const int p = p0 + (int)threadIdx.x;
-        const unsigned int cnt = p < P && st[p].status == ST_OK ? (st[p].n_gather + MX_M - 1) / MX_M : 0u;
+    for (int k0 = q0; k0 < q1; k0 += (int)blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        const int p = k < q1 ? (order ? order[k] : k) : 0;
+        const unsigned int cnt = k < q1 && st[p].status == ST_OK ? (st[p].n_gather + MX_M - 1) / MX_M : 0u;
         unsigned int incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -1134,7 +1136,7 @@ __global__ void k_gather_items(const PairState *__restrict__ st, int P, WorkItem
         }
         __syncthreads();
         const unsigned int at = base_s + warp_tot[wid] + incl - cnt;
-        for (unsigned int k = 0; k < cnt; ++k) items[at + k] = WorkItem{p, (int32_t)k, MODE_GATHER};
+        for (unsigned int t = 0; t < cnt; ++t) items[at + t] = WorkItem{p, (int32_t)t, MODE_GATHER};
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) base_s = at + cnt;
         __syncthreads();
@@ -1255,9 +1257,10 @@ cudaError_t launch_mixed(const MixedArgs &a, cudaStream_t s, std::string &err)
     return cudaGetLastError();
 }
 
-void launch_gather_items(const PairState *st, int P, WorkItem *items, unsigned int *n_items, cudaStream_t s)
+void launch_gather_items(const PairState *st, const int *order, int p0, int p1, WorkItem *items,
+                         unsigned int *n_items, cudaStream_t s)
 {
-    k_gather_items<<<1, 1024, 0, s>>>(st, P, items, n_items);
+    k_gather_items<<<1, 1024, 0, s>>>(st, order, p0, p1, items, n_items);
 }
 
 }  // namespace hb
