@@ -323,6 +323,48 @@ __device__ __forceinline__ unsigned short reflect_bf16_fast(float x, float ah, f
     return (unsigned short)(((__float_as_uint(V) & 0x80000000u) | (tr + (dist > 0.0f ? 0x10000u : 0u))) >> 16);
 }
 
+// Two elements of one row (columns e, e + 1; xw holds their BF16 values, the
+// lower column in the low half) with the operations of reflect_bf16_fast on
+// packed FP32 pairs: each half rounds exactly as the scalar form, so the
+// results and the `sure` decisions are the scalar ones.  Row constants: ah2,
+// nah2 = -ah2, al2 (splat), dl101 = dl * 1.01 rounded up; column pairs uh2,
+// ul2 and auh2 = |uh2|.  -P is not formed: fma(-ah, uh, P) = -Pe exactly, and
+// cross + Pe = cross - (-Pe).
+__device__ __forceinline__ uint32_t reflect_bf16_fast2(uint32_t xw, f2_t ah2, f2_t nah2, f2_t al2, f2_t dl101,
+                                                       f2_t uh2, f2_t ul2, f2_t auh2, bool &sure0, bool &sure1)
+{
+    const f2_t x2 = f2_pack(__uint_as_float(xw << 16), __uint_as_float(xw & 0xffff0000u));
+    const f2_t P = f2_mul(ah2, uh2), nPe = f2_fma(nah2, uh2, P);
+    const f2_t cross = f2_fma(ah2, ul2, f2_mul(al2, uh2));
+    const f2_t S = f2_add(x2, P), bp = f2_sub(S, x2);
+    const f2_t Se = f2_add(f2_sub(x2, f2_sub(S, bp)), f2_sub(P, bp));
+    const f2_t yl = f2_add(Se, f2_sub(cross, nPe));
+    const f2_t V = f2_add(S, yl), bv = f2_sub(V, S);
+    const f2_t t = f2_add(f2_sub(S, f2_sub(V, bv)), f2_sub(yl, bv));
+    const f2_t K = f2_fma_ru(auh2, dl101, f2_splat(0x1p-100f));
+    const f2_t E = f2_fma_ru(f2_add_ru(f2_abs(x2), f2_abs(P)), f2_splat(0x1p-43f), K);
+    const f2_t aV = f2_abs(V);
+    // per element: the truncated BF16 pattern, the midpoint above it, t signed like V
+    const uint32_t av0 = (uint32_t)aV, av1 = (uint32_t)(aV >> 32);
+    const uint32_t tr0 = av0 & 0xffff0000u, tr1 = av1 & 0xffff0000u;
+    const f2_t mid = ((f2_t)(tr1 | 0x8000u) << 32) | (tr0 | 0x8000u);
+    const f2_t ts = t ^ (V & 0x8000000080000000ull);
+    const f2_t dist = f2_add(f2_sub(aV, mid), ts);
+    const f2_t Eq = f2_mul_ru(E, f2_splat(1.0001f)), Et = f2_add_ru(E, f2_abs(t));
+    float d0, d1, e0, e1, q0, q1;
+    f2_unpack(dist, d0, d1);
+    f2_unpack(Eq, e0, e1);
+    f2_unpack(Et, q0, q1);
+    // a quarter of V's BF16 step: |v| stays between the neighbouring midpoints
+    const float s0 = __uint_as_float((av0 & 0x7f800000u) - (9u << 23)), s1 = __uint_as_float((av1 & 0x7f800000u) - (9u << 23));
+    sure0 = __uint_as_float(av0) >= 0x1p-100f && fabsf(d0) > e0 && q0 < s0;
+    sure1 = __uint_as_float(av1) >= 0x1p-100f && fabsf(d1) > e1 && q1 < s1;
+    const uint32_t v0 = (uint32_t)V, v1 = (uint32_t)(V >> 32);
+    const uint32_t z0 = ((v0 & 0x80000000u) | (tr0 + (d0 > 0.0f ? 0x10000u : 0u))) >> 16;
+    const uint32_t z1 = ((v1 & 0x80000000u) | (tr1 + (d1 > 0.0f ? 0x10000u : 0u))) >> 16;
+    return z0 | (z1 << 16);
+}
+
 // The exact FP64 dot product c = u^T x_r of the reference, a sequential FMA
 // chain over j = 0..d-1, for the rare elements a BF16-storage reflection cannot
 // decide from its compensated FP32 evaluation; -2c is kept in shared memory.
@@ -562,15 +604,20 @@ __global__ void __launch_bounds__(128, 4) k_reflect_v(const PairMeta *__restrict
         __syncthreads();
     }
 
-    // element pass: thread g < G owns columns 8g .. 8g + 7
+    // element pass: thread g < G owns columns 8g .. 8g + 7, two at a time on packed
+    // FP32 pairs (reflect_bf16_fast2)
     if (t < G) {
-        float uh[8], ul[8], mx[8], l1[8];
+        f2_t uh2[4], ul2[4], auh2[4];
+        float mx[8], l1[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            uh[e] = reflect ? uh_s[8 * t + e] : 0.0f;
-            ul[e] = reflect ? ul_s[8 * t + e] : 0.0f;
-            mx[e] = l1[e] = 0.0f;
+        for (int h = 0; h < 4; ++h) {
+            const int j = 8 * t + 2 * h;
+            uh2[h] = reflect ? f2_pack(uh_s[j], uh_s[j + 1]) : 0ull;
+            ul2[h] = reflect ? f2_pack(ul_s[j], ul_s[j + 1]) : 0ull;
+            auh2[h] = f2_abs(uh2[h]);
         }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) mx[e] = l1[e] = 0.0f;
         uint4 cur[RV_RB], nxt[RV_RB];
 #pragma unroll
         for (int k = 0; k < RV_RB; ++k) cur[k] = k < nr ? __ldg(src + (int64_t)k * G + t) : make_uint4(0u, 0u, 0u, 0u);
@@ -586,28 +633,36 @@ __global__ void __launch_bounds__(128, 4) k_reflect_v(const PairMeta *__restrict
                 if (r >= nr) break;
                 const uint32_t wv[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
                 uint32_t ow[4];
+                f2_t ah2 = 0ull, nah2 = 0ull, al2 = 0ull, dl101 = 0ull;
+                if (reflect) {
+                    ah2 = f2_splat(ah_s[r]);
+                    nah2 = f2_splat(-ah_s[r]);
+                    al2 = f2_splat(al_s[r]);
+                    dl101 = f2_splat(__fmul_ru(dl_s[r], 1.01f));
+                }
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    uint32_t zz[2];
+                    uint32_t zw = wv[h];  // the unreflected side keeps its values
+                    if (reflect) {
+                        bool s0, s1;
+                        zw = reflect_bf16_fast2(wv[h], ah2, nah2, al2, dl101, uh2[h], ul2[h], auh2[h], s0, s1);
+                        if (!s0)
+                            zw = (zw & 0xffff0000u) | reflect_v_fallback(ch.side ? pm.Y : pm.X, ch.row0 + r, r, d, up,
+                                                                         8 * t + 2 * h, wv[h] << 16, cs, chain_s);
+                        if (!s1)
+                            zw = (zw & 0xffffu) | (reflect_v_fallback(ch.side ? pm.Y : pm.X, ch.row0 + r, r, d, up,
+                                                                      8 * t + 2 * h + 1, wv[h] & 0xffff0000u, cs,
+                                                                      chain_s)
+                                                   << 16);
+                    }
 #pragma unroll
                     for (int s2 = 0; s2 < 2; ++s2) {
                         const int e = 2 * h + s2;
-                        const uint32_t xb = s2 ? (wv[h] & 0xffff0000u) : (wv[h] << 16);
-                        uint32_t zb = xb >> 16;
-                        if (reflect) {
-                            bool sure;
-                            zb = reflect_bf16_fast(__uint_as_float(xb), ah_s[r], al_s[r], dl_s[r], uh[e], ul[e],
-                                                   fabsf(uh[e]), sure);
-                            if (!sure)
-                                zb = reflect_v_fallback(ch.side ? pm.Y : pm.X, ch.row0 + r, r, d, up, 8 * t + e, xb, cs,
-                                                        chain_s);
-                        }
-                        const float zf = __uint_as_float(zb << 16);
+                        const float zf = __uint_as_float(s2 ? (zw & 0xffff0000u) : (zw << 16));
                         mx[e] = fmaxf(mx[e], fabsf(zf));
                         l1[e] = __fadd_ru(l1[e], fabsf(zf));
-                        zz[s2] = zb;
                     }
-                    ow[h] = zz[0] | (zz[1] << 16);
+                    ow[h] = zw;
                 }
                 dst[(int64_t)r * G + t] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
             }

@@ -388,33 +388,6 @@ __host__ __device__ __forceinline__ constexpr uint32_t idesc_bf16(int M, int N)
 }
 
 
-// Packed FP32 pairs (f32x2): two independent IEEE single-precision
-// operations, round to nearest, in one instruction; the low word is the
-// first element.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2_pack(float a, float b)
-{
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2_t v, float &a, float &b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
-{
-    f2_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
-{
-    f2_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 // The even-indexed bits of w to bits 0..15 and the odd-indexed ones to bits
 // 16..31, in order (four delta swaps: 2 <-> 1 within nibbles, then 2-bit,
 // nibble and byte fields).
