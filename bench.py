@@ -39,7 +39,7 @@ UNIT = "pair-tests/s"
 # profiles/k_mixed_traffic_batched256_d768.md).  Traffic grows with the tokens,
 # so a call moves this figure x sum(N).  It describes the kernel source it was
 # measured on: another hb_mixed.cu reports null until it is captured again.
-MIXED_TRAFFIC = {"source_sha256_prefix": "d2b8860d6c67a042", "bytes_per_token": 1265729024.0 / 238932}
+MIXED_TRAFFIC = {"source_sha256_prefix": "266af7aba4b0e9f5", "bytes_per_token": 1265745408.0 / 238932}
 WORKLOAD = ("batched: 4096 word pairs, n and m lognormal (median 300, sigma_log 1.0, clipped 20..8000), d=768 "
             "BF16, half null (sigma 0.35, random directions) / half alternative (sigma ratio 1.1), B=9999 each, "
             "Householder-aligned, two-sided log-volume statistic")
