@@ -121,6 +121,12 @@ def test_triage_gains_over_testing_every_pair(ctx):
     held_out = synth.workload_batched(seed=900, P=2048)
     TR.triage(ctx, net, held_out, opts, evaluate_all=False)  # warm-up: workspace sizing
     rep = TR.triage(ctx, net, held_out, opts)
+    # the timings are single calls of tens of milliseconds: take each leg's faster of two runs
+    rep2 = TR.triage(ctx, net, held_out, opts)
+    assert (rep2.skipped, rep2.decision_error_skipped) == (rep.skipped, rep.decision_error_skipped)
+    rep.seconds_features = min(rep.seconds_features, rep2.seconds_features)
+    rep.seconds_full_subset = min(rep.seconds_full_subset, rep2.seconds_full_subset)
+    rep.seconds_full_all = min(rep.seconds_full_all, rep2.seconds_full_all)
     print(f"\ntriage: loss {hist[0]:.4f} -> {hist[-1]:.4f}; {rep.skipped}/{rep.pairs} pairs skip the full test, "
           f"audit error {rep.audit_decision_error:.3f} ({rep.audited} audited), error on skipped pairs "
           f"{rep.decision_error_skipped:.4f}; features {rep.seconds_features:.3f} s + subset test "
