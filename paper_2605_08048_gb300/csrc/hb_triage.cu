@@ -44,14 +44,18 @@ __device__ __forceinline__ float block_sum(float v, float *red)
 // the w-th eighth of the columns j, lane (rq, cg) rows rq + 8i and columns
 // 4cg..4cg+3, then the 8 warp partials are summed; (2) W += Zc^T P: thread t
 // owns rows j = t + 256u of W, kept in registers for the whole pass.
-// Between passes W goes to shared memory (in the first chunk buffer) for the
-// orthonormalisation V = W R^-1 (Cholesky-QR of W^T W = R^T R).
+// Between passes W goes to shared memory (over both chunk buffers, which hold
+// at least d x 16 floats) for the orthonormalisation V = W R^-1 (Cholesky-QR
+// of W^T W = R^T R).  Chunks of 16 (BF16) or 8 (FP32) rows keep the shared
+// memory of a CTA near 110 KB and its registers at 128, so that two pairs'
+// CTAs share an SM and one's barriers and serial steps overlap the other's
+// streaming.
 // dynamic smem: Zc[2][R][ZS] (input element type), V[dp][16], part[8][R][16],
 // Pm[R][16]  (dp = d rounded up to 32, ZS = dp + 16 bytes of padding)
 // ---------------------------------------------------------------------------
 template <int DT> struct RitzTile;
 template <> struct RitzTile<DT_BF16> {
-    static constexpr int R = 32, ES = 2, PAD = 8;
+    static constexpr int R = 16, ES = 2, PAD = 8;
     __device__ __forceinline__ static void load4(const unsigned char *row, int j, float *z)
     {
         const uint2 w = *reinterpret_cast<const uint2 *>(row + 2 * j);
@@ -66,7 +70,7 @@ template <> struct RitzTile<DT_BF16> {
     }
 };
 template <> struct RitzTile<DT_F32> {
-    static constexpr int R = 16, ES = 4, PAD = 4;
+    static constexpr int R = 8, ES = 4, PAD = 4;
     __device__ __forceinline__ static void load4(const unsigned char *row, int j, float *z)
     {
         const float4 w = *reinterpret_cast<const float4 *>(row + 4 * j);
@@ -128,7 +132,7 @@ __device__ __forceinline__ void ritz_stage(unsigned char *buf, const void *Z, in
 }
 
 template <int DT, int JU>
-__global__ void __launch_bounds__(256, 1) k_ritz(const PairMeta *__restrict__ meta, const RunOpts o,
+__global__ void __launch_bounds__(256, 2) k_ritz(const PairMeta *__restrict__ meta, const RunOpts o,
                                                  const PairState *__restrict__ st, const void *__restrict__ Z,
                                                  float *__restrict__ lam_out)
 {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(256, 1) k_ritz(const PairMeta *__restrict__ me
     float *V = reinterpret_cast<float *>(sm_ritz + 2 * zc_bytes);
     float *part = V + (size_t)dp * RK;
     float *Pm = part + 8 * R * RK;
-    float *Wsm = reinterpret_cast<float *>(Zc[0]);  // W between passes, [d][16]
+    float *Wsm = reinterpret_cast<float *>(Zc[0]);  // W between passes, [d][16], over both chunk buffers
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, rq = lane >> 2, cg = lane & 3;
     const bool vec = (d * TT::ES) % 16 == 0;
 
@@ -215,10 +219,10 @@ __global__ void __launch_bounds__(256, 1) k_ritz(const PairMeta *__restrict__ me
             V[t] = v;
         }
         __syncthreads();
-        // the W staging overwrote the padding columns [d, dp) of chunk buffer 0
+        // the W staging overwrote the padding columns [d, dp) of both chunk buffers
         if (dp != d)
-            for (int t = tid; t < R * (dp - d); t += blockDim.x) {
-                const int r = t / (dp - d), j = d + t % (dp - d);
+            for (int t = tid; t < 2 * R * (dp - d); t += blockDim.x) {
+                const int r = t / (dp - d), j = d + t % (dp - d);  // r < 2R: rows of Zc[0] then Zc[1]
                 if (DT == DT_BF16) reinterpret_cast<unsigned short *>(Zc[0])[(size_t)r * ZS + j] = 0;
                 else reinterpret_cast<float *>(Zc[0])[(size_t)r * ZS + j] = 0.f;
             }
