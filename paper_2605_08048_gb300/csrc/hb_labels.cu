@@ -36,6 +36,14 @@ static LabelKeys label_keys(uint64_t seed, uint32_t stream)
     return k;
 }
 
+// a * b + c (mod 2^32) as one integer multiply-add
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // Walks relabelling b and hands each finished 32-bit word to `emit(w, word)`,
 // words in increasing order, each exactly once.  Each group of four positions
 // costs the counter multiply of round 0 and nine full rounds.
@@ -71,21 +79,19 @@ __device__ __forceinline__ void walk_labels(const LabelKeys &K, int n, int N, ui
         }
         uint32_t rem = (uint32_t)(N - i);
         uint32_t wd = 0;
+        // the bookkeeping of each decision (need -= t, wd += t 2^k) as integer
+        // multiply-adds, which run on the multiply pipe beside the logic pipe that
+        // the Philox rounds' XORs and the comparisons keep busy
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
             const uint4 w = draw((uint32_t)((i >> 2) + g));
-            uint32_t t = __umulhi(w.x, rem) < need;
-            need -= t;
-            wd |= t << (4 * g);
-            t = __umulhi(w.y, rem - 1u) < need;
-            need -= t;
-            wd |= t << (4 * g + 1);
-            t = __umulhi(w.z, rem - 2u) < need;
-            need -= t;
-            wd |= t << (4 * g + 2);
-            t = __umulhi(w.w, rem - 3u) < need;
-            need -= t;
-            wd |= t << (4 * g + 3);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t t = __umulhi(ws[k], rem - (uint32_t)k) < need;
+                need = imad(t, 0xffffffffu, need);
+                wd = imad(t, 1u << (4 * g + k), wd);
+            }
             rem -= 4u;
         }
         emit(i >> 5, wd);
