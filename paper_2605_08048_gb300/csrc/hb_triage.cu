@@ -101,25 +101,25 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// stage rows [r0, r0 + R) of the pair into a chunk buffer (rows past N read as zero)
-template <int DT>
+// stage rows [r0, r0 + ROWS) of the pair into a chunk buffer of row stride ZS
+// elements (rows past N read as zero)
+template <int DT, int ROWS>
 __device__ __forceinline__ void ritz_stage(unsigned char *buf, const void *Z, int64_t z_row, int r0, int N, int d,
-                                           bool vec)
+                                           int ZS, bool vec)
 {
-    using TT = RitzTile<DT>;
-    const int ZS = ritz_dp(d) + TT::PAD;
+    constexpr int ES = RitzTile<DT>::ES;
     const unsigned char *src = reinterpret_cast<const unsigned char *>(Z);
     if (vec) {  // rows of d elements are a whole number of 16-byte pieces
-        const int per_row = d * TT::ES / 16;
-        for (int t = threadIdx.x; t < TT::R * per_row; t += blockDim.x) {
+        const int per_row = d * ES / 16;
+        for (int t = threadIdx.x; t < ROWS * per_row; t += blockDim.x) {
             const int r = t / per_row, q = t - r * per_row;
             const bool in = r0 + r < N;
-            const unsigned char *g = in ? src + ((z_row + r0 + r) * (int64_t)d * TT::ES + (int64_t)q * 16) : src;
-            cp_async16(buf + (size_t)r * ZS * TT::ES + q * 16, g, in ? 16 : 0);
+            const unsigned char *g = in ? src + ((z_row + r0 + r) * (int64_t)d * ES + (int64_t)q * 16) : src;
+            cp_async16(buf + (size_t)r * ZS * ES + q * 16, g, in ? 16 : 0);
         }
         cp_async_commit();
     } else {
-        for (int t = threadIdx.x; t < TT::R * d; t += blockDim.x) {
+        for (int t = threadIdx.x; t < ROWS * d; t += blockDim.x) {
             const int r = t / d, j = t - r * d;
             const bool in = r0 + r < N;
             const uint32_t bits = in ? load_f32bits(Z, DT, (z_row + r0 + r) * (int64_t)d + j) : 0u;
@@ -128,6 +128,173 @@ __device__ __forceinline__ void ritz_stage(unsigned char *buf, const void *Z, in
             else
                 reinterpret_cast<uint32_t *>(buf)[(size_t)r * ZS + j] = bits;
         }
+    }
+}
+
+// the same for BF16 rows of a whole number of 16-byte pieces (per_row of
+// them), walking this thread's (row, piece) pairs by additions: (r, q) of item
+// t + k blockDim follows from that of item t (r0q, q0) and the step (dr, dq)
+__device__ __forceinline__ void ritz_stage_vec(unsigned char *buf, const unsigned char *src_row0, int rows_left,
+                                               int per_row, int ZS2, int64_t row_bytes, int r, int q, int dr, int dq,
+                                               int rows)
+{
+    for (; r < rows; r += dr, q += dq) {
+        if (q >= per_row) {
+            q -= per_row;
+            ++r;
+            if (r >= rows) break;
+        }
+        const bool in = r < rows_left;
+        const unsigned char *g = in ? src_row0 + r * row_bytes + q * 16 : src_row0;
+        cp_async16(buf + r * ZS2 + q * 16, g, in ? 16 : 0);
+    }
+    cp_async_commit();
+}
+
+// Cholesky-QR factor of W [d][16] (shared memory, 256 threads): G = W^T W =
+// R^T R, Rinv = R^-1 (upper triangular).  The Gram entries take one thread
+// each; the factorisation runs in warp 0 with lane c (lanes 16-31 repeat
+// lanes 0-15) holding column c of G in registers: right-looking Cholesky
+// (step k: r_kk = sqrt(G_kk), R_kc = G_kc / r_kk, G_ic -= R_ki R_kc for
+// i > k, R_ki taken from lane i), then R goes to Hm and lane c solves
+// R x = e_c by back substitution for column c of R^-1.  Ends with a barrier.
+__device__ void ritz_rinv(const float *Wsm, int d, float (*Hm)[RK], float (*Rinv)[RK])
+{
+    const int tid = threadIdx.x;
+    {
+        const int a = tid >> 4, bb = tid & 15;  // one Gram entry per thread
+        float g0 = 0.f, g1 = 0.f;
+        int j = 0;
+        for (; j + 1 < d; j += 2) {
+            g0 = fmaf(Wsm[j * RK + a], Wsm[j * RK + bb], g0);
+            g1 = fmaf(Wsm[(j + 1) * RK + a], Wsm[(j + 1) * RK + bb], g1);
+        }
+        if (j < d) g0 = fmaf(Wsm[j * RK + a], Wsm[j * RK + bb], g0);
+        Hm[a][bb] = g0 + g1;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int c = tid & 15;
+        float gc[RK];
+#pragma unroll
+        for (int i = 0; i < RK; ++i) gc[i] = Hm[i][c];
+#pragma unroll
+        for (int k = 0; k < RK; ++k) {
+            const float rkk = sqrtf(fmaxf(__shfl_sync(0xffffffffu, gc[k], k), 1e-30f));
+            const float rkc = c > k ? gc[k] / rkk : (c == k ? rkk : 0.f);  // R[k][c]
+            gc[k] = rkc;
+#pragma unroll
+            for (int i = k + 1; i < RK; ++i) gc[i] = fmaf(-__shfl_sync(0xffffffffu, rkc, i), rkc, gc[i]);
+        }
+        __syncwarp();  // every lane has read G
+        if (tid < 16)
+#pragma unroll
+            for (int i = 0; i < RK; ++i) Hm[i][c] = gc[i];
+        __syncwarp();
+        float x[RK];
+#pragma unroll
+        for (int i = RK - 1; i >= 0; --i) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = i + 1; k < RK; ++k) t = fmaf(Hm[i][k], x[k], t);
+            x[i] = i > c ? 0.f : (i == c ? 1.0f / Hm[i][i] : -t / Hm[i][i]);
+        }
+        if (tid < 16)
+#pragma unroll
+            for (int i = 0; i < RK; ++i) Rinv[i][c] = x[i];
+    }
+    __syncthreads();
+}
+
+// Eigenvalues of the 16 x 16 Rayleigh-Ritz matrix in Hm, by warp 0 (the
+// calling warp): symmetrise, then parallel cyclic Jacobi (round-robin order:
+// 15 rounds of 8 disjoint rotations per sweep) until the off-diagonal part is
+// negligible relative to the diagonal; lam[0..15] in descending order.
+__device__ void ritz_jacobi(float (*Hm)[RK], float *lam)
+{
+    __shared__ float jc[8], js[8];
+    __shared__ int ja[8], jb[8];
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < RK * RK; e += 32) {
+        const int a = e >> 4, b = e & 15;
+        if (a < b) Hm[a][b] = Hm[b][a] = 0.5f * (Hm[a][b] + Hm[b][a]);
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 20; ++sweep) {
+        float off = 0.f, dg = 0.f;
+        for (int e = lane; e < RK * RK; e += 32) {
+            const int a = e >> 4, b = e & 15;
+            const float h = Hm[a][b];
+            if (a < b) off += h * h;
+            if (a == b) dg += h * h;
+        }
+#pragma unroll
+        for (int s = 16; s; s >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, s);
+            dg += __shfl_xor_sync(0xffffffffu, dg, s);
+        }
+        if (off <= 1e-13f * dg || off < 1e-30f) break;
+        for (int k = 0; k < RK - 1; ++k) {
+            if (lane < 8) {
+                int a, b;
+                if (lane == 0) {
+                    a = k;
+                    b = RK - 1;
+                } else {
+                    a = (k + lane) % (RK - 1);
+                    b = (k - lane + RK - 1) % (RK - 1);
+                }
+                if (a > b) {
+                    const int tmp = a;
+                    a = b;
+                    b = tmp;
+                }
+                const float hab = Hm[a][b];
+                float c = 1.f, s = 0.f;
+                if (fabsf(hab) > 1e-30f) {
+                    const float theta = 0.5f * (Hm[b][b] - Hm[a][a]) / hab;
+                    const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+                    c = rsqrtf(t * t + 1.0f);
+                    s = t * c;
+                }
+                ja[lane] = a;
+                jb[lane] = b;
+                jc[lane] = c;
+                js[lane] = s;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // columns a, b of every row
+                const int task = lane + 32 * q, i = task >> 4, row = task & 15;
+                const int a = ja[i], b = jb[i];
+                const float c = jc[i], s = js[i];
+                const float hka = Hm[row][a], hkb = Hm[row][b];
+                Hm[row][a] = c * hka - s * hkb;
+                Hm[row][b] = s * hka + c * hkb;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // rows a, b of every column
+                const int task = lane + 32 * q, i = task >> 4, col = task & 15;
+                const int a = ja[i], b = jb[i];
+                const float c = jc[i], s = js[i];
+                const float hak = Hm[a][col], hbk = Hm[b][col];
+                Hm[a][col] = c * hak - s * hbk;
+                Hm[b][col] = s * hak + c * hbk;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        float ev[RK];
+        for (int a = 0; a < RK; ++a) ev[a] = Hm[a][a];
+        for (int a = 1; a < RK; ++a)  // insertion sort, descending
+            for (int b = a; b > 0 && ev[b] > ev[b - 1]; --b) {
+                const float tmp = ev[b];
+                ev[b] = ev[b - 1];
+                ev[b - 1] = tmp;
+            }
+        for (int a = 0; a < RK; ++a) lam[a] = ev[a];
     }
 }
 
@@ -141,8 +308,6 @@ __global__ void __launch_bounds__(256, 2) k_ritz(const PairMeta *__restrict__ me
     extern __shared__ __align__(16) unsigned char sm_ritz[];
     __shared__ float Hm[RK][RK];
     __shared__ float Rinv[RK][RK];
-    __shared__ float jc[8], js[8];
-    __shared__ int ja[8], jb[8];
     const int p = blockIdx.x;
     if (st[p].status != ST_OK) {
         if (threadIdx.x < RK) lam_out[p * RK + threadIdx.x] = 0.f;
@@ -174,44 +339,7 @@ __global__ void __launch_bounds__(256, 2) k_ritz(const PairMeta *__restrict__ me
     const float invN = 1.0f / (float)N;
     for (int iter = 0; iter <= RITZ_ITERS; ++iter) {
         // ---- V = orth(W): G = W^T W = R^T R (Cholesky), V = W R^-1 ----
-        {
-            const int a = tid >> 4, bb = tid & 15;  // one Gram entry per thread
-            float g0 = 0.f, g1 = 0.f;
-            int j = 0;
-            for (; j + 1 < d; j += 2) {
-                g0 = fmaf(Wsm[j * RK + a], Wsm[j * RK + bb], g0);
-                g1 = fmaf(Wsm[(j + 1) * RK + a], Wsm[(j + 1) * RK + bb], g1);
-            }
-            if (j < d) g0 = fmaf(Wsm[j * RK + a], Wsm[j * RK + bb], g0);
-            Hm[a][bb] = g0 + g1;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            float Rm[RK][RK];
-            for (int i = 0; i < RK; ++i)
-                for (int k = 0; k < RK; ++k) Rm[i][k] = 0.f;
-            for (int k = 0; k < RK; ++k) {  // G = R^T R, R upper triangular
-                float s = Hm[k][k];
-                for (int i = 0; i < k; ++i) s -= Rm[i][k] * Rm[i][k];
-                const float rkk = sqrtf(fmaxf(s, 1e-30f));
-                Rm[k][k] = rkk;
-                for (int c = k + 1; c < RK; ++c) {
-                    float t = Hm[k][c];
-                    for (int i = 0; i < k; ++i) t -= Rm[i][k] * Rm[i][c];
-                    Rm[k][c] = t / rkk;
-                }
-            }
-            for (int c = RK - 1; c >= 0; --c) {  // R^-1, upper triangular
-                for (int i = 0; i < RK; ++i) Rinv[i][c] = 0.f;
-                Rinv[c][c] = 1.0f / Rm[c][c];
-                for (int i = c - 1; i >= 0; --i) {
-                    float t = 0.f;
-                    for (int k = i + 1; k <= c; ++k) t += Rm[i][k] * Rinv[k][c];
-                    Rinv[i][c] = -t / Rm[i][i];
-                }
-            }
-        }
-        __syncthreads();
+        ritz_rinv(Wsm, d, Hm, Rinv);
         for (int t = tid; t < d * RK; t += blockDim.x) {
             const int j = t >> 4, c = t & 15;
             float v = 0.f;
@@ -234,11 +362,11 @@ __global__ void __launch_bounds__(256, 2) k_ritz(const PairMeta *__restrict__ me
         for (int u = 0; u < JU; ++u)
 #pragma unroll
             for (int c = 0; c < RK; ++c) Wacc[u][c] = 0.f;
-        ritz_stage<DT>(Zc[0], Z, pm.z_row, 0, N, d, vec);
+        ritz_stage<DT, R>(Zc[0], Z, pm.z_row, 0, N, d, ZS, vec);
         for (int ch = 0; ch < nch; ++ch) {
             if (vec) cp_async_wait_all();
             __syncthreads();  // chunk ch landed; everyone is done with chunk ch - 1
-            if (ch + 1 < nch) ritz_stage<DT>(Zc[(ch + 1) & 1], Z, pm.z_row, (ch + 1) * R, N, d, vec);
+            if (ch + 1 < nch) ritz_stage<DT, R>(Zc[(ch + 1) & 1], Z, pm.z_row, (ch + 1) * R, N, d, ZS, vec);
             const unsigned char *zc = Zc[ch & 1];
             // (1) warp partial of P = Zc V over columns [w dp/8, (w+1) dp/8)
             {
@@ -324,91 +452,254 @@ __global__ void __launch_bounds__(256, 2) k_ritz(const PairMeta *__restrict__ me
         Hm[a][bb] = h0 + h1;
     }
     __syncthreads();
-    if (w != 0) return;
-    // warp 0: symmetrise, then parallel cyclic Jacobi (round-robin order: 15
-    // rounds of 8 disjoint rotations per sweep) until the off-diagonal part is
-    // negligible relative to the diagonal
-    for (int e = lane; e < RK * RK; e += 32) {
-        const int a = e >> 4, b = e & 15;
-        if (a < b) Hm[a][b] = Hm[b][a] = 0.5f * (Hm[a][b] + Hm[b][a]);
+    if (w == 0) ritz_jacobi(Hm, lam_out + (size_t)p * RK);
+}
+
+// ---------------------------------------------------------------------------
+// BF16 Ritz values on the warp-level tensor-core MMA (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation), one CTA (256 threads, 8 warps) per pair.
+//
+// The contraction is skinny (16 columns), so the MMA's role is to take the
+// 2 x 16 FMAs of every element of Z off the FP32 pipe; tcgen05 tiles
+// (128 rows x N >= 16, operands through shared-memory descriptors) would
+// read the same operands at no higher rate for N = 16.  Z is exact in BF16;
+// the other factor of each product (V in P = Zc V, P in W += Zc^T P) is split
+// into a BF16 pair x = hi + lo, hi = rn(x), lo = rn(x - hi), which carries
+// about 16 significant bits, and both halves go through the MMA into the same
+// FP32 accumulator.  Chunks of 16 rows; warp w owns the K range (columns of
+// Z) [128 w KS / 8 ... ) in P = Zc V (its partial tile is summed with the
+// others through shared memory) and the same rows of W, kept in registers for
+// the whole pass.  dpm = d rounded up to 128 (= 128 KS); columns [d, dpm) of
+// the chunk buffers and of V stay zero.
+// dynamic smem: Zc[2][16][ZS] BF16, Vh/Vl[16][ZS] BF16 (V transposed),
+// part[8][16][16] FP32, Ph/Pl[16][24] BF16  (ZS = dpm + 8)
+// ---------------------------------------------------------------------------
+constexpr int RM_R = 16;   // rows per chunk
+constexpr int RM_PS = 24;  // row stride of the P tiles in BF16 elements (48 B: ldmatrix rows on distinct banks)
+
+__host__ __device__ __forceinline__ int ritz_dpm(int d) { return (d + 127) & ~127; }
+
+__host__ __device__ __forceinline__ size_t ritz_mma_smem(int d)
+{
+    const size_t zs = (size_t)ritz_dpm(d) + 8;
+    return 2 * RM_R * zs * 2 + 2 * RK * zs * 2 + sizeof(float) * 8 * RM_R * RK + 2 * RM_R * RM_PS * 2;
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// c += A (16 x 16, row) B (16 x 8, col), BF16 operands, FP32 accumulator
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void bf16_split(float x, unsigned short &hi, unsigned short &lo)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(unsigned short b) { return __uint_as_float((uint32_t)b << 16); }
+
+template <int KS>
+__global__ void __launch_bounds__(256, 2) k_ritz_mma(const PairMeta *__restrict__ meta, const RunOpts o,
+                                                     const PairState *__restrict__ st, const void *__restrict__ Z,
+                                                     float *__restrict__ lam_out)
+{
+    constexpr int dpm = 128 * KS, ZS = dpm + 8;
+    constexpr size_t zc_bytes = (size_t)RM_R * ZS * 2;
+    extern __shared__ __align__(16) unsigned char sm_ritz[];
+    __shared__ float Hm[RK][RK];
+    __shared__ float Rinv[RK][RK];
+    const int p = blockIdx.x;
+    if (st[p].status != ST_OK) {
+        if (threadIdx.x < RK) lam_out[p * RK + threadIdx.x] = 0.f;
+        return;
     }
-    __syncwarp();
-    for (int sweep = 0; sweep < 20; ++sweep) {
-        float off = 0.f, dg = 0.f;
-        for (int e = lane; e < RK * RK; e += 32) {
-            const int a = e >> 4, b = e & 15;
-            const float h = Hm[a][b];
-            if (a < b) off += h * h;
-            if (a == b) dg += h * h;
-        }
-#pragma unroll
-        for (int s = 16; s; s >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, s);
-            dg += __shfl_xor_sync(0xffffffffu, dg, s);
-        }
-        if (off <= 1e-13f * dg || off < 1e-30f) break;
-        for (int k = 0; k < RK - 1; ++k) {
-            if (lane < 8) {
-                int a, b;
-                if (lane == 0) {
-                    a = k;
-                    b = RK - 1;
-                } else {
-                    a = (k + lane) % (RK - 1);
-                    b = (k - lane + RK - 1) % (RK - 1);
-                }
-                if (a > b) {
-                    const int tmp = a;
-                    a = b;
-                    b = tmp;
-                }
-                const float hab = Hm[a][b];
-                float c = 1.f, s = 0.f;
-                if (fabsf(hab) > 1e-30f) {
-                    const float theta = 0.5f * (Hm[b][b] - Hm[a][a]) / hab;
-                    const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-                    c = rsqrtf(t * t + 1.0f);
-                    s = t * c;
-                }
-                ja[lane] = a;
-                jb[lane] = b;
-                jc[lane] = c;
-                js[lane] = s;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {  // columns a, b of every row
-                const int task = lane + 32 * q, i = task >> 4, row = task & 15;
-                const int a = ja[i], b = jb[i];
-                const float c = jc[i], s = js[i];
-                const float hka = Hm[row][a], hkb = Hm[row][b];
-                Hm[row][a] = c * hka - s * hkb;
-                Hm[row][b] = s * hka + c * hkb;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {  // rows a, b of every column
-                const int task = lane + 32 * q, i = task >> 4, col = task & 15;
-                const int a = ja[i], b = jb[i];
-                const float c = jc[i], s = js[i];
-                const float hak = Hm[a][col], hbk = Hm[b][col];
-                Hm[a][col] = c * hak - s * hbk;
-                Hm[b][col] = s * hak + c * hbk;
-            }
-            __syncwarp();
-        }
+    const PairMeta pm = meta[p];
+    const int d = o.d, N = pm.N;
+    unsigned char *Zc[2] = {sm_ritz, sm_ritz + zc_bytes};
+    unsigned short *Vh = reinterpret_cast<unsigned short *>(sm_ritz + 2 * zc_bytes);
+    unsigned short *Vl = Vh + (size_t)RK * ZS;
+    float *part = reinterpret_cast<float *>(Vl + (size_t)RK * ZS);
+    unsigned short *Ph = reinterpret_cast<unsigned short *>(part + 8 * RM_R * RK);
+    unsigned short *Pl = Ph + RM_R * RM_PS;
+    float *Wsm = reinterpret_cast<float *>(Zc[0]);  // W between passes, [d][16], over both chunk buffers
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, tig = lane & 3;
+    const int li = lane >> 3, lr = lane & 7;  // ldmatrix: this lane's matrix and row
+    const bool vec = (d * 2) % 16 == 0;
+    // staging walk of this thread (vector rows): item tid + 256 k is row r, piece q
+    const int per_row = d / 8, st_dr = 256 / per_row, st_dq = 256 % per_row;
+    const int st_r = tid / per_row, st_q = tid % per_row;
+    const int64_t row_bytes = (int64_t)d * 2;
+    const unsigned char *zrow0 = reinterpret_cast<const unsigned char *>(Z) + pm.z_row * row_bytes;
+    const uint32_t zc_s0 = (uint32_t)__cvta_generic_to_shared(Zc[0]);
+    const uint32_t vh_s = (uint32_t)__cvta_generic_to_shared(Vh), vl_s = (uint32_t)__cvta_generic_to_shared(Vl);
+    const uint32_t ph_s = (uint32_t)__cvta_generic_to_shared(Ph), pl_s = (uint32_t)__cvta_generic_to_shared(Pl);
+
+    // zero the chunk buffers and V once: columns [d, dpm) of V stay zero
+    for (size_t t = tid; t < (2 * zc_bytes + 2 * (size_t)RK * ZS * 2) / 4; t += blockDim.x)
+        reinterpret_cast<float *>(sm_ritz)[t] = 0.f;
+    __syncthreads();
+    // fixed start block: (w >> 8) / 2^24 - 1/2, w = Philox(j, c, 0x5EED, 0; key 0, 0) word 0
+    for (int t = tid; t < d * RK; t += blockDim.x) {
+        const int j = t >> 4, c = t & 15;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)c, 0x5EEDu, 0u), 0u, 0u);
+        Wsm[t] = (float)(r.x >> 8) * (1.0f / 16777216.0f) - 0.5f;
     }
-    if (lane == 0) {
-        float ev[RK];
-        for (int a = 0; a < RK; ++a) ev[a] = Hm[a][a];
-        for (int a = 1; a < RK; ++a)  // insertion sort, descending
-            for (int b = a; b > 0 && ev[b] > ev[b - 1]; --b) {
-                const float tmp = ev[b];
-                ev[b] = ev[b - 1];
-                ev[b - 1] = tmp;
+    __syncthreads();
+    const int nch = (N + RM_R - 1) / RM_R;
+    const float invN = 1.0f / (float)N;
+    for (int iter = 0; iter <= RITZ_ITERS; ++iter) {
+        // ---- V = orth(W) = W R^-1, stored transposed as BF16 pairs ----
+        ritz_rinv(Wsm, d, Hm, Rinv);
+        for (int t = tid; t < d * RK; t += blockDim.x) {
+            const int j = t >> 4, c = t & 15;
+            float v = 0.f;
+            for (int k = 0; k <= c; ++k) v = fmaf(Wsm[j * RK + k], Rinv[k][c], v);
+            bf16_split(v, Vh[c * ZS + j], Vl[c * ZS + j]);
+        }
+        __syncthreads();
+        // the W staging overwrote columns [d, dpm) of the chunk rows
+        if (dpm != d)
+            for (int t = tid; t < 2 * RM_R * (dpm - d); t += blockDim.x) {
+                const int r = t / (dpm - d), j = d + t % (dpm - d);  // r < 32: rows of Zc[0] then Zc[1]
+                reinterpret_cast<unsigned short *>(Zc[0])[(size_t)r * ZS + j] = 0;
             }
-        for (int a = 0; a < RK; ++a) lam_out[p * RK + a] = ev[a];
+        __syncthreads();
+
+        // ---- one pass: W = Z^T (Z V) / N ----
+        float wacc[KS][2][4];
+#pragma unroll
+        for (int m = 0; m < KS; ++m)
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) wacc[m][n][q] = 0.f;
+        if (vec) ritz_stage_vec(Zc[0], zrow0, N, per_row, ZS * 2, row_bytes, st_r, st_q, st_dr, st_dq, RM_R);
+        else ritz_stage<DT_BF16, RM_R>(Zc[0], Z, pm.z_row, 0, N, d, ZS, vec);
+        for (int ch = 0; ch < nch; ++ch) {
+            if (vec) cp_async_wait_all();
+            __syncthreads();  // chunk ch landed; everyone is done with chunk ch - 1 and the P tiles
+            if (ch + 1 < nch) {
+                const int r0 = (ch + 1) * RM_R;
+                if (vec)
+                    ritz_stage_vec(Zc[(ch + 1) & 1], zrow0 + r0 * row_bytes, N - r0, per_row, ZS * 2, row_bytes,
+                                   st_r, st_q, st_dr, st_dq, RM_R);
+                else
+                    ritz_stage<DT_BF16, RM_R>(Zc[(ch + 1) & 1], Z, pm.z_row, r0, N, d, ZS, vec);
+            }
+            const uint32_t zs = zc_s0 + (uint32_t)((ch & 1) * zc_bytes);
+            // (1) this warp's partial of P = Zc V over its K range
+            {
+                float pacc[4][4];  // n-tile 0 hi, lo, n-tile 1 hi, lo: four independent MMA chains
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) pacc[i][q] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    const int k0 = (w * KS + ks) * 16;
+                    uint32_t a[4], bh[4], bl[4];
+                    // A = Zc[0:16, k0:k0+16]: matrices (rows 0-7 | 8-15) x (cols k0 | k0 + 8)
+                    ldsm_x4(zs + (uint32_t)((((li & 1) * 8 + lr) * ZS + k0 + (li >> 1) * 8) * 2), a);
+                    // B = V[k0:k0+16, 0:16] from V^T: matrices (n 0-7 | 8-15) x (k0 | k0 + 8)
+                    const uint32_t vo = (uint32_t)((((li >> 1) * 8 + lr) * ZS + k0 + (li & 1) * 8) * 2);
+                    ldsm_x4(vh_s + vo, bh);
+                    ldsm_x4(vl_s + vo, bl);
+                    mma_bf16_16816(pacc[0], a, bh[0], bh[1]);
+                    mma_bf16_16816(pacc[1], a, bl[0], bl[1]);
+                    mma_bf16_16816(pacc[2], a, bh[2], bh[3]);
+                    mma_bf16_16816(pacc[3], a, bl[2], bl[3]);
+                }
+                // partial tile, columns of rows with bit 1 of the row set swapped by 8 halves (rows g and
+                // g + 2 would share banks): stored at col ^ 8 ((row >> 1) & 1)
+                float *pw = part + w * (RM_R * RK);
+                const int sw = ((g >> 1) & 1) << 3;  // rows g and g + 8 have the same swap
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    const int c = (n * 8 + 2 * tig) ^ sw;
+                    *reinterpret_cast<float2 *>(pw + g * RK + c) =
+                        make_float2(pacc[2 * n][0] + pacc[2 * n + 1][0], pacc[2 * n][1] + pacc[2 * n + 1][1]);
+                    *reinterpret_cast<float2 *>(pw + (g + 8) * RK + c) =
+                        make_float2(pacc[2 * n][2] + pacc[2 * n + 1][2], pacc[2 * n][3] + pacc[2 * n + 1][3]);
+                }
+            }
+            __syncthreads();
+            {  // P = sum of the 8 partials (one entry per thread), as a BF16 pair
+                const int r = tid >> 4, c = tid & 15, e = r * RK + (c ^ (((r >> 1) & 1) << 3));
+                float s = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < 8; ++ww) s += part[ww * RM_R * RK + e];
+                bf16_split(s, Ph[r * RM_PS + c], Pl[r * RM_PS + c]);
+            }
+            __syncthreads();
+            // (2) W += Zc^T P for this warp's rows of W
+            uint32_t bh[4], bl[4];
+            {  // B = P[0:16, 0:16]: matrices (t 0-7 | 8-15) x (n 0-7 | 8-15), transposed on load
+                const uint32_t po = (uint32_t)((((li & 1) * 8 + lr) * RM_PS + (li >> 1) * 8) * 2);
+                ldsm_x4_t(ph_s + po, bh);
+                ldsm_x4_t(pl_s + po, bl);
+            }
+#pragma unroll
+            for (int mt = 0; mt < KS; ++mt) {
+                const int j0 = (w * KS + mt) * 16;
+                uint32_t a[4];
+                // A = Zc^T[j0:j0+16, 0:16]: matrices (j0 | j0 + 8) x (t 0-7 | 8-15), transposed on load
+                ldsm_x4_t(zs + (uint32_t)((((li >> 1) * 8 + lr) * ZS + j0 + (li & 1) * 8) * 2), a);
+                mma_bf16_16816(wacc[mt][0], a, bh[0], bh[1]);
+                mma_bf16_16816(wacc[mt][0], a, bl[0], bl[1]);
+                mma_bf16_16816(wacc[mt][1], a, bh[2], bh[3]);
+                mma_bf16_16816(wacc[mt][1], a, bl[2], bl[3]);
+            }
+        }
+        __syncthreads();  // all reads of the chunk buffers done
+#pragma unroll
+        for (int mt = 0; mt < KS; ++mt) {
+            const int j = (w * KS + mt) * 16 + g;
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const int c = n * 8 + 2 * tig;
+                if (j < d)
+                    *reinterpret_cast<float2 *>(Wsm + j * RK + c) =
+                        make_float2(wacc[mt][n][0] * invN, wacc[mt][n][1] * invN);
+                if (j + 8 < d)
+                    *reinterpret_cast<float2 *>(Wsm + (j + 8) * RK + c) =
+                        make_float2(wacc[mt][n][2] * invN, wacc[mt][n][3] * invN);
+            }
+        }
+        __syncthreads();
     }
+    // Rayleigh-Ritz: H = V^T W (V orthonormal, W = S V), one entry per thread
+    {
+        const int a = tid >> 4, bb = tid & 15;
+        float h0 = 0.f, h1 = 0.f;
+        for (int j = 0; j < d; ++j) {
+            h0 = fmaf(bf16_bits_to_float(Vh[a * ZS + j]), Wsm[j * RK + bb], h0);
+            h1 = fmaf(bf16_bits_to_float(Vl[a * ZS + j]), Wsm[j * RK + bb], h1);
+        }
+        Hm[a][bb] = h0 + h1;
+    }
+    __syncthreads();
+    if (w == 0) ritz_jacobi(Hm, lam_out + (size_t)p * RK);
 }
 
 __global__ void k_features_pack(const PairMeta *__restrict__ meta, int P, const RunOpts o,
@@ -676,11 +967,32 @@ static void launch_ritz_ju(const PairMeta *meta, int P, const RunOpts &o, const 
     }
 }
 
+template <int KS>
+static void launch_ritz_mma(const PairMeta *meta, int P, const RunOpts &o, const PairState *st, const void *Z,
+                            float *lam, cudaStream_t s)
+{
+    const size_t smem = ritz_mma_smem(o.d);
+    cudaFuncSetAttribute(k_ritz_mma<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ritz_mma<KS><<<P, 256, smem, s>>>(meta, o, st, Z, lam);
+}
+
 void launch_features(const PairMeta *meta, int P, const RunOpts &o, const PairState *st, const void *Z, float *lam,
                      float *feat, double *tobs, cudaStream_t s)
 {
-    if (o.dtype == DT_F32) launch_ritz_ju<DT_F32>(meta, P, o, st, Z, lam, s);
-    else launch_ritz_ju<DT_BF16>(meta, P, o, st, Z, lam, s);
+    if (o.dtype == DT_F32) {
+        launch_ritz_ju<DT_F32>(meta, P, o, st, Z, lam, s);
+    } else {
+        switch (ritz_dpm(o.d) / 128) {  // K steps of 16 per warp; d <= 1024 is checked by the caller
+        case 1: launch_ritz_mma<1>(meta, P, o, st, Z, lam, s); break;
+        case 2: launch_ritz_mma<2>(meta, P, o, st, Z, lam, s); break;
+        case 3: launch_ritz_mma<3>(meta, P, o, st, Z, lam, s); break;
+        case 4: launch_ritz_mma<4>(meta, P, o, st, Z, lam, s); break;
+        case 5: launch_ritz_mma<5>(meta, P, o, st, Z, lam, s); break;
+        case 6: launch_ritz_mma<6>(meta, P, o, st, Z, lam, s); break;
+        case 7: launch_ritz_mma<7>(meta, P, o, st, Z, lam, s); break;
+        default: launch_ritz_mma<8>(meta, P, o, st, Z, lam, s); break;
+        }
+    }
     k_features_pack<<<(P + 127) / 128, 128, 0, s>>>(meta, P, o, st, lam, feat, tobs);
 }
 

@@ -163,7 +163,7 @@ def evaluate_at_scale(ctx: H.Context, train_pairs: int = 200_000, eval_pairs: in
     decision error and the time the triage saves.  Returns the totals."""
     from . import synth
 
-    opts = opts or H.make_opts(B=9999, seed=1)
+    opts = opts or H.make_opts(B=9999, seed=1, path=H.HB_PATH_MIXED_2SM)
     say = log or (lambda *_: None)
     t0 = time.perf_counter()
     feats, targets = [], []

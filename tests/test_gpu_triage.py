@@ -30,9 +30,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("d,dtype", [(768, "bf16"), (100, "bf16"), (1000, "f32"), (250, "f32"), (1024, "bf16")],
-                         ids=["768-bf16", "100-bf16-unaligned-rows", "1000-f32", "250-f32-unaligned-rows",
-                              "1024-bf16"])
+@pytest.mark.parametrize("d,dtype", [(768, "bf16"), (100, "bf16"), (300, "bf16"), (1000, "f32"), (250, "f32"),
+                                     (1024, "bf16")],
+                         ids=["768-bf16", "100-bf16-unaligned-rows", "300-bf16-unaligned-rows", "1000-f32",
+                              "250-f32-unaligned-rows", "1024-bf16"])
 def test_features_match_oracle(ctx, d, dtype):
     b = synth.batch(61, 4, d=d, dtype=dtype, sizes=([120, 300, 45, 800], [200, 90, 60, 700]))
     f, tobs, res = H.triage_features(ctx, _dev(b.XY), b.n, b.m, H.make_opts())
@@ -47,9 +48,10 @@ def test_features_match_oracle(ctx, d, dtype):
         assert abs(f[p, 18] - want[18]) < 1e-5
 
 
-def test_null_quantiles_match_oracle(ctx):
+@pytest.mark.parametrize("path", [H.HB_PATH_MIXED, H.HB_PATH_MIXED_2SM], ids=["mixed", "mixed-2sm"])
+def test_null_quantiles_match_oracle(ctx, path):
     b = synth.batch(62, 3, d=128, dtype="bf16", sizes=([40, 150, 77], [60, 90, 33]))
-    q, res = H.null_quantiles(ctx, _dev(b.XY), b.n, b.m, H.make_opts(B=2000, seed=4))
+    q, res = H.null_quantiles(ctx, _dev(b.XY), b.n, b.m, H.make_opts(B=2000, seed=4, path=path))
     q = q.cpu().numpy().astype(np.float64)
     for p in range(3):
         X, Y = b.pair(p)
@@ -119,7 +121,7 @@ def test_triage_skips_the_full_test_for_most_pairs(ctx):
     triage (features included) is faster than testing every pair depends on
     how fast the full test is against the feature pass; the times are printed,
     not asserted."""
-    opts = H.make_opts(B=9999, seed=1)
+    opts = H.make_opts(B=9999, seed=1, path=H.HB_PATH_MIXED_2SM)
     train_b = [synth.workload_batched(seed=500 + k, P=1024) for k in range(8)]
     feat, target = TR.training_set(ctx, train_b, opts)
     net, hist = TR.train(ctx, feat, target, epochs=80, batch=1024, lr=2e-3)
