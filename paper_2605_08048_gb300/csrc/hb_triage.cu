@@ -37,7 +37,9 @@ __device__ __forceinline__ float block_sum(float v, float *red)
 }
 
 // ---------------------------------------------------------------------------
-// Ritz values of Z^T Z / N, one CTA (256 threads, 8 warps) per pair.
+// Ritz values of Z^T Z / N, one CTA (256 threads, 8 warps) per pair, FP32
+// SIMT (FP32 rows; BF16 rows take k_ritz_mma below, which keeps the same
+// chunk loop and replaces the FMAs of both contractions by MMAs).
 //
 // One pass W = Z^T (Z V) streams Z through shared memory in chunks of R rows
 // (cp.async double buffer).  Per chunk: (1) P = Zc V (R x 16): warp w takes
@@ -46,10 +48,9 @@ __device__ __forceinline__ float block_sum(float v, float *red)
 // owns rows j = t + 256u of W, kept in registers for the whole pass.
 // Between passes W goes to shared memory (over both chunk buffers, which hold
 // at least d x 16 floats) for the orthonormalisation V = W R^-1 (Cholesky-QR
-// of W^T W = R^T R).  Chunks of 16 (BF16) or 8 (FP32) rows keep the shared
-// memory of a CTA near 110 KB and its registers at 128, so that two pairs'
-// CTAs share an SM and one's barriers and serial steps overlap the other's
-// streaming.
+// of W^T W = R^T R).  Chunks of 8 FP32 rows keep the shared memory of a CTA
+// near 110 KB and its registers at 128, so that two pairs' CTAs share an SM
+// and one's barriers and serial steps overlap the other's streaming.
 // dynamic smem: Zc[2][R][ZS] (input element type), V[dp][16], part[8][R][16],
 // Pm[R][16]  (dp = d rounded up to 32, ZS = dp + 16 bytes of padding)
 // ---------------------------------------------------------------------------
