@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: the test-suite and the smoke check may import this
 module; the product path never does.  It shares no code with the CUDA
 kernels.  The paper has no learned component; these definitions are the
-task's triage model, written out plainly:
+library's triage model, written out plainly:
 
 - features: log n, log m, log(d * lambda_k) for the 16 Ritz values lambda_k of
   the pooled scatter Z^T Z / N after a fixed number of block subspace

@@ -1,5 +1,5 @@
-// hb_triage.cu -- kernels of the learned triage (a task component; the paper
-// has no learned part): per-pair features, the 19 -> 256 -> 256 -> 9 MLP that
+// hb_triage.cu -- kernels of the learned triage (an addition of this library;
+// the paper has no learned part): per-pair features, the 19 -> 256 -> 256 -> 9 MLP that
 // predicts null quantiles of |T| (forward, backward, pinball loss, Adam),
 // null-quantile targets from the method's own relabellings, and the
 // predicted p used to route pairs.
